@@ -1,0 +1,245 @@
+"""Pins of the oracle's Lanczos recursions and spectrum (CPU only).
+
+P3  closed-form independent-particle chi0 (kernel off) vs Lanczos + spectrum
+P4  direct resolvent chi = w u^H (omega + i eta - L)^{-1} v by dense solves
+P5  moments: w n0 sum_i conj(z_i) (T^k e1)_i = w u^H L^k v for k < 10
+P6  non-Hermitian and pseudo-Hermitian chains give the same chi at convergence
+P7  biorthogonality p_i^H q_j = delta_ij (NH, and PHM with p = J L q) and
+    q_i^H J q_j = s_i delta_ij (PH, relative to ||q_i|| ||q_j||: the indefinite
+    metric loses it quickly, which is recorded, not hidden)
+P8  collinear special case ([H, S_z] = 0): chi_xz = chi_zx = 0, chi_xx = chi_yy,
+    chi_xy = -chi_yx
+P9  sum rule: int chi d omega = -i pi w u^H v (residue sum)
+P12 Lanczos on the dense brute-force L equals the matrix-free chain step by step
+Plus Thomas elimination vs pivoted banded LAPACK.
+"""
+
+import numpy as np
+import pytest
+
+from _cases import ground_state, liouvillian, particle_hole
+from oracle.lanczos import lanczos_nh, lanczos_ph, lanczos_phm, run_chain
+from oracle.liouvillian import jdot
+from oracle.spectrum import HA_MEV, chi_banded, chi_thomas
+
+OMEGAS = np.linspace(0.0, 0.3, 31)
+
+
+def _direct(ph, lv, mu, omegas, eta):
+    va, _ = ph.from_br(lv.start_vector(mu))
+    ua = [ph.from_br(lv.left_vector(l))[0] for l in range(3)]
+    w = lv.gs.wk[0]
+    out = np.zeros((3, len(omegas)), dtype=np.complex128)
+    for i, om in enumerate(omegas):
+        y = np.linalg.solve((om + 1j * eta) * np.eye(ph.dim) - ph.L, va)
+        for l in range(3):
+            out[l, i] = w * np.vdot(ua[l], y)
+    return out
+
+
+@pytest.fixture(scope="module")
+def c0_chains():
+    lv = liouvillian("C0")
+    return {f: [run_chain(lv, mu, 800 if f != "phm" else 600, f, keep_basis=20) for mu in range(3)]
+            for f in ("nh", "ph", "phm")}
+
+
+@pytest.mark.parametrize("flavor", ["nh", "phm"])
+def test_p4_direct_resolvent(c0_chains, flavor):
+    lv, ph = liouvillian("C0"), particle_hole("C0")
+    eta = 10.0 / HA_MEV
+    for mu in (0, 2):
+        ref = _direct(ph, lv, mu, OMEGAS, eta)
+        got = chi_thomas(c0_chains[flavor][mu], OMEGAS, eta, lv.gs.wk[0])
+        assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref[mu])
+
+
+def test_p6_nh_equals_ph(c0_chains):
+    lv, ph = liouvillian("C0"), particle_hole("C0")
+    eta = 0.1
+    for mu in range(3):
+        ref = _direct(ph, lv, mu, OMEGAS, eta)
+        x_nh = chi_thomas(c0_chains["nh"][mu], OMEGAS, eta, lv.gs.wk[0])
+        x_ph = chi_thomas(c0_chains["ph"][mu], OMEGAS, eta, lv.gs.wk[0])
+        x_pm = chi_thomas(c0_chains["phm"][mu], OMEGAS, eta, lv.gs.wk[0])
+        nrm = np.linalg.norm(ref[mu])
+        assert np.linalg.norm(x_nh - ref) <= 1e-8 * nrm
+        assert np.linalg.norm(x_ph - ref) <= 1e-8 * nrm
+        assert np.linalg.norm(x_pm - ref) <= 1e-8 * nrm
+        assert np.linalg.norm(x_ph - x_nh) <= 1e-8 * nrm
+
+
+@pytest.mark.parametrize("flavor", ["nh", "ph", "phm"])
+def test_p5_moments(c0_chains, flavor):
+    lv = liouvillian("C0")
+    w = lv.gs.wk[0]
+    for mu in range(3):
+        c = c0_chains[flavor][mu]
+        m = 40
+        t = np.diag(c.alpha[:m]) + np.diag(c.beta[:m - 1], -1) + np.diag(c.gamma[:m - 1], 1)
+        v = lv.start_vector(mu)
+        u = [lv.left_vector(l) for l in range(3)]
+        e = np.zeros(m, dtype=np.complex128)
+        e[0] = 1.0
+        lkv = v.copy()
+        for k in range(10):
+            for l in range(3):
+                lhs = w * c.n0 * np.vdot(c.z[l, :m], e)
+                rhs = w * np.vdot(u[l], lkv)
+                # scale: |w| ||u|| ||L^k v|| (the moments themselves can cancel)
+                scale = w * np.linalg.norm(u[l]) * np.linalg.norm(lkv)
+                assert abs(lhs - rhs) <= 1e-10 * scale
+            e = t @ e
+            lkv = lv.apply(lkv)
+
+
+def test_p7_biorthogonality(c0_chains):
+    for mu in range(3):
+        nh = c0_chains["nh"][mu]
+        g = np.array([[np.vdot(p, q) for q in nh.basis_q] for p in nh.basis_p])
+        assert np.max(np.abs(g - np.eye(len(nh.basis_q)))) <= 1e-10
+        pm = c0_chains["phm"][mu]
+        g = np.array([[np.vdot(p, q) for q in pm.basis_q] for p in pm.basis_p])
+        assert np.max(np.abs(g - np.eye(len(pm.basis_q)))) <= 1e-10
+        ph = c0_chains["ph"][mu]
+        k = 8
+        nq = np.array([np.linalg.norm(q) for q in ph.basis_q[:k]])
+        gj = np.array([[jdot(qi, qj) for qj in ph.basis_q[:k]] for qi in ph.basis_q[:k]])
+        assert np.max(np.abs(gj - np.diag(ph.signs[:k])) / np.outer(nq, nq)) <= 1e-8
+        # the PH recursion's alpha is real in exact arithmetic (J L is Hermitian on range(P_c))
+        assert np.max(np.abs(ph.alpha.imag)) == 0.0
+
+
+def test_p12_dense_vs_matrix_free():
+    """NH and PHM agree step by step to rounding over 50 steps.  The J-metric PH
+    is compared on the longitudinal chain (mu = z): for the transverse chains the
+    start vector has nearly equal X and Y weight, ||q_1|| ~ 30 at unit J-norm, and
+    r = L q - alpha q - gamma q' cancels catastrophically (alpha ~ +-200), so two
+    correct codes part after a few steps; that conditioning is a property of the
+    indefinite metric, not of either code."""
+    lv, ph = liouvillian("C0"), particle_hole("C0")
+    v = lv.start_vector(1)
+    u = [lv.left_vector(l) for l in range(3)]
+    va = ph.from_br(v)[0]
+    ua = [ph.from_br(x)[0] for x in u]
+    for flavor in ("nh", "ph", "phm"):
+        if flavor == "nh":
+            m, tol = 50, 1e-12
+            a = lanczos_nh(lv.apply, lv.apply_adjoint, v, u, m)
+            b = lanczos_nh(lambda x: ph.L @ x, lambda x: ph.L.conj().T @ x, va, ua, m)
+        elif flavor == "phm":
+            m, tol = 50, 1e-12
+            a = lanczos_phm(lv.apply, v, u, m)
+            b = lanczos_phm_dense(ph.L, ph.J, va, ua, m)
+        else:
+            m, tol = 20, 1e-10
+            vz = lv.start_vector(2)
+            a = lanczos_ph(lv.apply, vz, u, m)
+            b = lanczos_ph_dense(ph.L, ph.J, ph.from_br(vz)[0], ua, m)
+        for fa, fb in ((a.alpha, b.alpha), (a.beta, b.beta), (a.gamma, b.gamma), (a.z, b.z)):
+            assert np.max(np.abs(fa - fb)) <= tol * np.max(np.abs(fb))
+
+
+def lanczos_phm_dense(lmat, jvec, v, u, m):
+    """Standard Hermitian Lanczos for L in the metric H = J L, written with explicit H."""
+    hmat = jvec[:, None] * lmat
+    n0 = np.sqrt(np.vdot(v, hmat @ v).real)
+    q, qp, b = v / n0, np.zeros_like(v), 0.0
+    from oracle.lanczos import Coefficients
+    al, be = np.zeros(m, complex), np.zeros(m)
+    z = np.zeros((3, m), complex)
+    for j in range(m):
+        a = lmat @ q
+        al[j] = np.vdot(q, hmat @ a).real
+        z[:, j] = [np.vdot(q, x) for x in u]
+        r = a - al[j] * q - b * qp
+        be[j] = np.sqrt(np.vdot(r, hmat @ r).real)
+        qp, q, b = q, r / be[j], be[j]
+    return Coefficients(al, be, be.astype(complex), z, n0, m, "ok")
+
+
+def lanczos_ph_dense(lmat, jvec, v, u, m):
+    """The same J-metric recursion written on the dense particle-hole basis."""
+    c0 = np.vdot(v, jvec * v).real
+    n0 = np.sqrt(abs(c0))
+    s = np.sign(c0)
+    q, qp, g = v / n0, np.zeros_like(v), 0.0
+    from oracle.lanczos import Coefficients
+    al, be, ga = np.zeros(m, complex), np.zeros(m), np.zeros(m, complex)
+    z = np.zeros((3, m), complex)
+    for j in range(m):
+        a = lmat @ q
+        al[j] = s * np.vdot(q, jvec * a).real
+        z[:, j] = [np.vdot(q, x) for x in u]
+        r = a - al[j] * q - g * qp
+        c = np.vdot(r, jvec * r).real
+        be[j] = np.sqrt(abs(c))
+        sn = np.sign(c)
+        ga[j] = s * sn * be[j]
+        qp, q, s, g = q, r / be[j], sn, ga[j]
+    return Coefficients(al, be, ga, z, n0, m, "ok")
+
+
+@pytest.mark.parametrize("flavor", ["nh", "ph", "phm"])
+def test_p3_chi0_closed_form(flavor):
+    gs = ground_state("C0", 0)
+    lv, ph = liouvillian("C0", 0), particle_hole("C0", 0)
+    eta = 10.0 / HA_MEV
+    w = gs.wk[0]
+    mu = 0
+    # closed form: w sum [<U|s_l|phi><phi|s_m|U>/(w+ieta-D^X) - (same on Y)/(w+ieta+D^Y)]
+    va = ph.from_br(lv.start_vector(mu))[0]
+    ua = [ph.from_br(lv.left_vector(l))[0] for l in range(3)]
+    ref = np.zeros((3, len(OMEGAS)), dtype=np.complex128)
+    for i, om in enumerate(OMEGAS):
+        den = (om + 1j * eta) - ph.J * ph.D
+        for l in range(3):
+            ref[l, i] = w * np.sum(np.conj(ua[l]) * va / den)
+    c = run_chain(lv, mu, 700, flavor)
+    got = chi_thomas(c, OMEGAS, eta, w)
+    tol = 1e-4 if flavor == "ph" else 1e-8
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref[mu])
+
+
+def test_thomas_matches_banded(c0_chains):
+    """Unpivoted Thomas vs pivoted banded LU.  They agree to rounding for the
+    symmetric (PHM) and NH tridiagonals; the J-metric T alternates sign and is
+    ill-conditioned without pivoting, so there only 1e-5 holds (the pivoted solve
+    is the primary one, ``chi``)."""
+    lv = liouvillian("C0")
+    for flavor, tol in (("nh", 1e-12), ("phm", 1e-12), ("ph", 1e-5)):
+        c = c0_chains[flavor][0]
+        for eta in (10.0 / HA_MEV, 0.05):
+            a = chi_thomas(c, OMEGAS, eta, lv.gs.wk[0], m=300)
+            b = chi_banded(c, OMEGAS, eta, lv.gs.wk[0], m=300)
+            assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b))
+
+
+def test_p8_collinear_symmetry():
+    lv = liouvillian("C0", 3, True)
+    eta = 0.05
+    chi = np.array([chi_thomas(run_chain(lv, mu, 300, "nh"), OMEGAS, eta, lv.gs.wk[0])
+                    for mu in range(3)])  # chi[mu][lam]
+    scale = np.abs(chi).max()
+    assert np.abs(chi[2][0]).max() <= 1e-12 * scale and np.abs(chi[0][2]).max() <= 1e-12 * scale
+    assert np.abs(chi[2][1]).max() <= 1e-12 * scale and np.abs(chi[1][2]).max() <= 1e-12 * scale
+    assert np.abs(chi[0][0] - chi[1][1]).max() <= 1e-8 * scale
+    assert np.abs(chi[1][0] + chi[0][1]).max() <= 1e-8 * scale
+
+
+def test_p9_sum_rule():
+    """int_{-R}^{R} chi d omega -> -i pi w u^H v; the 1/omega tails leave a real
+    remainder -2 w u^H L v / R (first moment), which is added back."""
+    lv = liouvillian("C0")
+    c = run_chain(lv, 0, 600, "nh")
+    w = lv.gs.wk[0]
+    eta = 0.05
+    u = [lv.left_vector(l) for l in range(3)]
+    v = lv.start_vector(0)
+    exact = -1j * np.pi * w * np.array([np.vdot(x, v) for x in u])
+    assert np.allclose(exact, -1j * np.pi * w * c.n0 * np.conj(c.z[:, 0]), rtol=1e-12)
+    first = w * np.vdot(u[0], lv.apply(v))
+    r = 400.0
+    om = np.linspace(-r, r, 160001)
+    integ = np.trapezoid(chi_thomas(c, om, eta, w), om, axis=1)
+    assert abs(integ[0] + 2.0 * first / r - exact[0]) <= 1e-4 * abs(exact[0])
