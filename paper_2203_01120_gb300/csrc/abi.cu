@@ -1,0 +1,302 @@
+// extern "C" entry points of include/tdlz.h.  Every call validates its
+// arguments on the host, runs inside a try block and maps failures to a
+// tdlz_status with a message for tdlz_last_error(); no C++ exception crosses
+// the boundary.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lanczos.cuh"
+#include "spectrum.cuh"
+
+using namespace tdlz;
+
+namespace tdlz {
+std::atomic<long long> g_launches{0};
+}
+
+struct tdlz_ctx {
+  Context c;
+};
+struct tdlz_chain {
+  tdlz_ctx *owner;
+  ChainSet set;
+};
+
+namespace {
+
+tdlz_status fail(tdlz_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->c.last_error = msg;
+  return (tdlz_status)code;
+}
+
+template <class F>
+tdlz_status guarded(tdlz_ctx *ctx, F &&f) {
+  if (!ctx) return TDLZ_ERR_ARG;
+  try {
+    TDLZ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    f();
+    ctx->c.last_error.clear();
+    return TDLZ_OK;
+  } catch (const Error &e) {
+    return fail(ctx, e.status, e.msg);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, TDLZ_ERR_OOM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(ctx, TDLZ_ERR_STATE, e.what());
+  }
+}
+
+QSlot &slot_of(tdlz_ctx *ctx, int qslot) {
+  TDLZ_REQUIRE(qslot >= 0 && qslot < (int)ctx->c.slots.size() && ctx->c.slots[qslot],
+               TDLZ_ERR_ARG, "invalid q-slot");
+  return *ctx->c.slots[qslot];
+}
+
+}  // namespace
+
+extern "C" {
+
+tdlz_status tdlz_create(tdlz_ctx **out, int device, void *cuda_stream) {
+  if (!out) return TDLZ_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    (void)cudaGetLastError();
+    return TDLZ_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return TDLZ_ERR_ARG;
+  tdlz_ctx *ctx = new (std::nothrow) tdlz_ctx();
+  if (!ctx) return TDLZ_ERR_OOM;
+  ctx->c.device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return TDLZ_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    ctx->c.stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return TDLZ_ERR_CUDA;
+    }
+    ctx->c.own_stream = true;
+  }
+  *out = ctx;
+  return TDLZ_OK;
+}
+
+void tdlz_destroy(tdlz_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  ctx->c.slots.clear();
+  if (ctx->c.own_stream) cudaStreamDestroy(ctx->c.stream);
+  delete ctx;
+}
+
+const char *tdlz_last_error(const tdlz_ctx *ctx) {
+  return ctx ? ctx->c.last_error.c_str() : "NULL context";
+}
+
+tdlz_status tdlz_profile(tdlz_ctx *ctx, int enable) {
+  return guarded(ctx, [&] {
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+    ctx->c.prof.reset();
+    ctx->c.prof.on = enable != 0;
+  });
+}
+
+tdlz_status tdlz_profile_read(tdlz_ctx *ctx, double *ms, int64_t *launches, double *bytes,
+                              double *flops) {
+  return guarded(ctx, [&] {
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+    Profiler &p = ctx->c.prof;
+    p.flush();
+    for (int i = 0; i < ST_COUNT; ++i) {
+      if (ms) ms[i] = p.ms[i];
+      if (launches) launches[i] = p.launches[i];
+      if (bytes) bytes[i] = p.bytes[i];
+      if (flops) flops[i] = p.flops[i];
+    }
+  });
+}
+
+const char *tdlz_stage_name(int stage) { return stage_name(stage); }
+
+int64_t tdlz_launch_count(void) { return g_launches.load(); }
+
+tdlz_status tdlz_synchronize(tdlz_ctx *ctx) {
+  return guarded(ctx, [&] { TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream)); });
+}
+
+tdlz_status tdlz_load_ground_state(tdlz_ctx *ctx, const tdlz_ground_state *gs, int *qslot) {
+  return guarded(ctx, [&] {
+    TDLZ_REQUIRE(qslot != nullptr, TDLZ_ERR_ARG, "qslot output pointer is NULL");
+    auto s = std::make_unique<QSlot>();
+    load_slot(ctx->c, *s, gs);
+    ctx->c.slots.push_back(std::move(s));
+    *qslot = (int)ctx->c.slots.size() - 1;
+  });
+}
+
+tdlz_status tdlz_vec_layout(const tdlz_ctx *cctx, int qslot, int64_t *nelem, int *npwx) {
+  tdlz_ctx *ctx = const_cast<tdlz_ctx *>(cctx);
+  return guarded(ctx, [&] {
+    QSlot &s = slot_of(ctx, qslot);
+    if (nelem) *nelem = s.br_elems();
+    if (npwx) *npwx = s.npwx;
+  });
+}
+
+tdlz_status tdlz_apply_liouvillian(tdlz_ctx *ctx, int qslot, const void *x, void *y, int adjoint,
+                                   int precision) {
+  return guarded(ctx, [&] {
+    QSlot &s = slot_of(ctx, qslot);
+    TDLZ_REQUIRE(x && y, TDLZ_ERR_ARG, "x and y must be device pointers");
+    TDLZ_REQUIRE(precision == TDLZ_FP64 || precision == TDLZ_MIXED, TDLZ_ERR_ARG,
+                 "precision must be TDLZ_FP64 or TDLZ_MIXED");
+    size_t bytes = (size_t)s.br_elems() * (precision == TDLZ_FP64 ? 16 : 8);
+    const char *xa = (const char *)x;
+    const char *ya = (const char *)y;
+    TDLZ_REQUIRE(xa + bytes <= ya || ya + bytes <= xa, TDLZ_ERR_ARG, "x and y overlap");
+    cudaPointerAttributes at{};
+    TDLZ_REQUIRE(cudaPointerGetAttributes(&at, x) == cudaSuccess &&
+                     (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged),
+                 TDLZ_ERR_ARG, "x is not device memory");
+    TDLZ_REQUIRE(cudaPointerGetAttributes(&at, y) == cudaSuccess &&
+                     (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged),
+                 TDLZ_ERR_ARG, "y is not device memory");
+    if (precision == TDLZ_FP64)
+      apply_liouvillian<double>(ctx->c, s, (const double2 *)x, (double2 *)y, adjoint != 0);
+    else
+      apply_liouvillian<float>(ctx->c, s, (const float2 *)x, (float2 *)y, adjoint != 0);
+  });
+}
+
+tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_chain **out) {
+  tdlz_chain *ch = nullptr;
+  tdlz_status st = guarded(ctx, [&] {
+    TDLZ_REQUIRE(p && out, TDLZ_ERR_ARG, "NULL params or output");
+    TDLZ_REQUIRE(p->nchain >= 1 && p->nsteps >= 1, TDLZ_ERR_ARG, "nchain and nsteps must be >= 1");
+    TDLZ_REQUIRE(p->flavor >= 0 && p->flavor <= 2, TDLZ_ERR_ARG, "unknown flavour");
+    TDLZ_REQUIRE(p->precision == TDLZ_FP64 || p->precision == TDLZ_MIXED, TDLZ_ERR_ARG,
+                 "unknown precision");
+    TDLZ_REQUIRE(p->qslot && p->mu, TDLZ_ERR_ARG, "NULL qslot / mu arrays");
+    for (int c = 0; c < p->nchain; ++c) {
+      slot_of(ctx, p->qslot[c]);
+      TDLZ_REQUIRE(p->mu[c] >= 0 && p->mu[c] <= 2, TDLZ_ERR_ARG, "mu must be 0, 1 or 2");
+    }
+    ch = new tdlz_chain();
+    ch->owner = ctx;
+    ch->set.ctx = &ctx->c;
+    ch->set.flavor = p->flavor;
+    ch->set.precision = p->precision;
+    ch->set.cap = p->nsteps;
+    ch->set.chains.resize(p->nchain);
+    for (int c = 0; c < p->nchain; ++c) {
+      ch->set.chains[c].qslot = p->qslot[c];
+      ch->set.chains[c].mu = p->mu[c];
+    }
+    ch->set.init();
+  });
+  if (st != TDLZ_OK) {
+    delete ch;
+    ch = nullptr;
+  }
+  if (out) *out = ch;
+  return st;
+}
+
+tdlz_status tdlz_chain_advance(tdlz_chain *ch, int nsteps) {
+  if (!ch) return TDLZ_ERR_ARG;
+  return guarded(ch->owner, [&] {
+    TDLZ_REQUIRE(nsteps >= 0, TDLZ_ERR_ARG, "nsteps must be >= 0");
+    ch->set.advance(nsteps);
+  });
+}
+
+tdlz_status tdlz_chain_read(tdlz_chain *ch, tdlz_lanczos_result *res) {
+  if (!ch) return TDLZ_ERR_ARG;
+  return guarded(ch->owner, [&] {
+    TDLZ_REQUIRE(res != nullptr, TDLZ_ERR_ARG, "NULL result");
+    ch->set.read(res);
+  });
+}
+
+void tdlz_chain_destroy(tdlz_chain *ch) {
+  if (!ch) return;
+  cudaSetDevice(ch->owner->c.device);
+  cudaStreamSynchronize(ch->owner->c.stream);
+  delete ch;
+}
+
+tdlz_status tdlz_lanczos_run(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_lanczos_result *res) {
+  tdlz_chain *ch = nullptr;
+  tdlz_status st = tdlz_chain_create(ctx, p, &ch);
+  if (st != TDLZ_OK) return st;
+  st = tdlz_chain_advance(ch, p->nsteps);
+  if (st == TDLZ_OK) st = tdlz_chain_read(ch, res);
+  tdlz_chain_destroy(ch);
+  return st;
+}
+
+tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectrum_params *sp,
+                          double *chi, int *nomega) {
+  return guarded(ctx, [&] {
+    TDLZ_REQUIRE(c && sp && nomega, TDLZ_ERR_ARG, "NULL coefficients, parameters or nomega");
+    TDLZ_REQUIRE(c->nchain >= 1 && c->nsteps >= 1, TDLZ_ERR_ARG, "empty coefficient set");
+    TDLZ_REQUIRE(c->steps && c->alpha && c->beta && c->gamma && c->z && c->n0 && c->wk,
+                 TDLZ_ERR_ARG, "NULL coefficient array");
+    TDLZ_REQUIRE(sp->step > 0 && sp->end >= sp->start && std::isfinite(sp->eta) && sp->eta > 0,
+                 TDLZ_ERR_ARG, "need step > 0, end >= start and eta > 0");
+    TDLZ_REQUIRE(sp->units == 0 || sp->units == 1, TDLZ_ERR_ARG, "units must be 0 (Ha) or 1 (meV)");
+    long long nw = (long long)std::floor((sp->end - sp->start) / sp->step + 0.5) + 1;
+    TDLZ_REQUIRE(nw >= 1 && nw <= (1 << 24), TDLZ_ERR_ARG, "frequency grid too long");
+    *nomega = (int)nw;
+    if (!chi) return;
+    for (int i = 0; i < c->nchain; ++i)
+      TDLZ_REQUIRE(c->steps[i] >= 0 && c->steps[i] <= c->nsteps, TDLZ_ERR_ARG,
+                   "steps out of range");
+    const double conv = sp->units == 1 ? 1.0 / 27211.386245988 : 1.0;
+    const int nc = c->nchain, cap = c->nsteps;
+    DevBuf d_steps, d_al, d_be, d_ga, d_z, d_n0, d_wk, d_chi, d_scr;
+    cudaStream_t st = ctx->c.stream;
+    auto up = [&](DevBuf &b, const void *src, size_t bytes) {
+      b.alloc(bytes);
+      TDLZ_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+    };
+    up(d_steps, c->steps, sizeof(int) * nc);
+    up(d_al, c->alpha, sizeof(double2) * nc * cap);
+    up(d_be, c->beta, sizeof(double) * nc * cap);
+    up(d_ga, c->gamma, sizeof(double2) * nc * cap);
+    up(d_z, c->z, sizeof(double2) * nc * 3 * cap);
+    up(d_n0, c->n0, sizeof(double) * nc);
+    up(d_wk, c->wk, sizeof(double) * nc);
+    d_chi.alloc(sizeof(double2) * nc * 3 * nw);
+    d_scr.alloc(sizeof(double2) * 4 * (size_t)cap * nc * nw);
+    SpecArgs a{};
+    a.nchain = nc;
+    a.nomega = (int)nw;
+    a.cap = cap;
+    a.steps = d_steps.as<int>();
+    a.alpha = d_al.as<double2>();
+    a.beta = d_be.as<double>();
+    a.gamma = d_ga.as<double2>();
+    a.z = d_z.as<double2>();
+    a.n0 = d_n0.as<double>();
+    a.wk = d_wk.as<double>();
+    a.start = sp->start * conv;
+    a.step = sp->step * conv;
+    a.eta = sp->eta * conv;
+    a.scratch = d_scr.as<double2>();
+    a.chi = d_chi.as<double2>();
+    launch_spectrum(st, a);
+    TDLZ_CUDA_TRY(cudaMemcpyAsync(chi, d_chi.p, sizeof(double2) * nc * 3 * nw,
+                                  cudaMemcpyDeviceToHost, st));
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Internal state of the tdlz library: per-q-slot ground-state data resident in
+// HBM, the Liouvillian workspaces, and the kernels' host-side entry points.
+#pragma once
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/tdlz.h"
+#include "common.cuh"
+#include "fft.cuh"
+#include "profile.cuh"
+
+namespace tdlz {
+
+// Device buffer owned by the library (cudaMalloc / cudaFree).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) {
+      reset();
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { reset(); }
+  void alloc(size_t n) {
+    reset();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw Error{TDLZ_ERR_OOM, "cudaMalloc(" + std::to_string(n) + " bytes) failed: " +
+                                    cudaGetErrorString(e)};
+    }
+    bytes = n;
+  }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class U> U *as() const { return reinterpret_cast<U *>(p); }
+};
+
+// Ground-state data of one precision (T = double or float) on the device.
+template <class T> struct SlotData {
+  DevBuf ukq;    // [2][nk][nb][2][npwx] occupied k+q spinors (P_c)
+  DevBuf ur;     // [2][nk][nb][2][Nr]   occupied k orbitals in real space
+  DevBuf beta;   // [nk][nproj][npwx]
+  DevBuf dnl;    // [2nproj][2nproj]
+  DevBuf kin;    // [nk][npwx]  |k+q+G|^2/2   (real)
+  DevBuf evals;  // [2][nk][nb]               (real)
+  DevBuf vloc;   // [Nr]   (real)
+  DevBuf bfield; // [3][Nr] (real)
+  DevBuf fxc;    // [10][Nr] (real)
+  DevBuf vhfac;  // [Nr]   4 pi / |q+G|^2 / Nr on the Hartree sphere (real)
+  DevBuf wk;     // [nk]   (real)
+  DevBuf uvec;   // [3][BR] u^lambda = J sigma^lambda U (unprojected)
+  bool ready = false;
+};
+
+template <class T> struct Workspace {
+  DevBuf xr;    // [2][nk][nb][2][Nr] real-space response orbitals
+  DevBuf rho;   // [4][Nr]
+  DevBuf vpot;  // [4][Nr]
+  DevBuf hgrid; // [Nr] Hartree scratch
+  DevBuf h;     // [BR] sphere intermediate
+  DevBuf xin;   // [BR] sign-flipped input for the adjoint
+  DevBuf proj;  // [2nk][nproj][2nb]  <beta|x>
+  DevBuf dmix;  // [2nk][2nb][nproj]
+  DevBuf ovl;   // [2nk][nb][nb]      <U_kq|h>
+  DevBuf part;  // split-K partial sums
+  bool ready = false;
+};
+
+struct QSlot {
+  int fft[3];
+  long long nr;
+  int nk, nb, npwx, nproj, kernel_mask;
+  double omega;
+  double q[3];
+  std::vector<int> npw_k, npw_kq;
+  std::vector<double> wk;
+  DevBuf idx_k, idx_kq;  // [nk][npwx] int32 grid index (-1 beyond npw)
+  DevBuf map_kq_k;       // [nk][npwx] int32: index of the same G in the k sphere or -1
+  DevBuf npwkq_d;        // [nk] int32
+  DevBuf coeff_k;        // [2][nk][nb][2][npwx] occupied k spinors (FP64; start vectors)
+  FFTPlan plan;
+  SlotData<double> d64;
+  SlotData<float> d32;
+  Workspace<double> w64;
+  Workspace<float> w32;
+  long long br_elems() const { return 2LL * nk * nb * 2 * npwx; }
+  long long rows() const { return 2LL * nk * nb * 2; }
+  ~QSlot() { plan.release(); }
+};
+
+struct Context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  std::vector<std::unique_ptr<QSlot>> slots;
+  Profiler prof;
+};
+
+template <class T> inline SlotData<T> &slot_data(QSlot &s) {
+  if constexpr (sizeof(T) == 8)
+    return s.d64;
+  else
+    return s.d32;
+}
+template <class T> inline Workspace<T> &slot_ws(QSlot &s) {
+  if constexpr (sizeof(T) == 8)
+    return s.w64;
+  else
+    return s.w32;
+}
+
+// --- Liouvillian (liouvillian.cu) ---
+template <class T> void ensure_precision(Context &ctx, QSlot &s);
+template <class T>
+void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool adjoint);
+template <class T> void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v);
+void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs);
+
+// --- vector helpers (lanczos.cu) ---
+template <class T>
+void jflip_copy(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y);
+
+inline unsigned blocks_for(long long n, int t = 256) {
+  long long b = (n + t - 1) / t;
+  if (b > 2147483647LL) b = 2147483647LL;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace tdlz

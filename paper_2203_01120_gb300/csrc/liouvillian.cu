@@ -1,0 +1,872 @@
+// The Liouvillian of the batch representation on the GPU.
+//
+// y = L x with x = (X, Y) on the k+q spheres (Eq. Liouvillian_BR_q and the
+// block actions after it):
+//   out_X =  P_{k+q}  [ (H+_{k+q} - e_{n,k}) x_n + V'_HXC U_{n,k} ]
+//   out_Y = -P+_{k+q} [ (H-_{k+q} - e_{n,k}) y_n + V'+_HXC (TU)_{n,k} ]
+// Stages (one launch each, every band-side of every k batched together):
+//   1  scatter x onto the grid, inverse 3D FFT          -> x(r)          (all band-sides)
+//   2  response densities n', m' (Eqs. charge_dens_resp_q, spin_dens_resp_q)
+//   3  Hartree at q (Eq. v_H_q): FFT, 4 pi/|q+G|^2, inverse FFT
+//   4  ALSDA kernel v'_a = d_a0 v'_H + f_ab rho'_b (Eqs. v_XC_q, b_XC_q)
+//   5  [v_loc + s B.sigma] x(r) + W^s U(r) (W^X = v0 + v.sigma, W^Y = v0 - v.sigma)
+//   6  forward 3D FFT, gather to the k+q sphere, + (|k+q+G|^2/2 - e_n) x
+//   7  V_NL: <beta|x> (split-K reduction GEMM), D mixing, beta (D <beta|x>)
+//   8  P_c: <U_m|h> (split-K reduction GEMM), h - U <U|h>, row sign (Y side -)
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "engine.cuh"
+
+namespace tdlz {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+
+// ------------------------------------------------------------ grid <-> sphere
+template <class T>
+__global__ void scatter_rows_kernel(const cx<T> *__restrict__ x, cx<T> *__restrict__ grid,
+                                    const int *__restrict__ idx, int nk, int nb, int npwx,
+                                    long long nr, T scale, long long nrows) {
+  long long row = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+  if (row >= nrows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npwx; g += gridDim.x * blockDim.x) {
+    int ig = idx[(long long)k * npwx + g];
+    if (ig >= 0) grid[row * nr + ig] = cscale<T>(x[row * npwx + g], scale);
+  }
+}
+
+// h = scale * grid[G] + (kin - e_n) x  on the k+q sphere; zero padding.
+template <class T>
+__global__ void gather_rows_kernel(const cx<T> *__restrict__ grid, const cx<T> *__restrict__ x,
+                                   cx<T> *__restrict__ h, const int *__restrict__ idx,
+                                   const T *__restrict__ kin, const T *__restrict__ evals, int nk,
+                                   int nb, int npwx, long long nr, T scale, long long nrows) {
+  long long row = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+  if (row >= nrows) return;
+  long long band = row / 2;  // (side, k, n)
+  int k = (int)((band / nb) % nk);
+  T e = evals[band];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npwx; g += gridDim.x * blockDim.x) {
+    int ig = idx[(long long)k * npwx + g];
+    cx<T> out = czero<T>();
+    if (ig >= 0) {
+      cx<T> gv = grid[row * nr + ig];
+      cx<T> xv = x[row * npwx + g];
+      T d = kin[(long long)k * npwx + g] - e;
+      out = mk<T>(gv.x * scale + d * xv.x, gv.y * scale + d * xv.y);
+    }
+    h[row * npwx + g] = out;
+  }
+}
+
+inline dim3 row_grid(long long nrows, int npwx) {
+  unsigned bx = (unsigned)((npwx + kThreads - 1) / kThreads);
+  long long y = nrows, z = 1;
+  while (y > 65535) {
+    z *= 2;
+    y = (nrows + z - 1) / z;
+  }
+  return dim3(bx, (unsigned)y, (unsigned)z);
+}
+
+// ------------------------------------------------------------- density (a3)
+// rho'_a(r) = sum_k w_k sum_n [ U^X_n^+ s_a x_n + t_a U^Y_n^+ s_a y_n ],
+// t = (1,-1,-1,-1); fixed summation order (deterministic).
+template <class T>
+__global__ void density_kernel(const cx<T> *__restrict__ ur, const cx<T> *__restrict__ xr,
+                               const T *__restrict__ wk, cx<T> *__restrict__ rho, int nk, int nb,
+                               long long nr) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+       r += (long long)gridDim.x * blockDim.x) {
+    cx<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+    for (int side = 0; side < 2; ++side) {
+      T t = side == 0 ? T(1) : T(-1);
+      for (int k = 0; k < nk; ++k) {
+        cx<T> a0 = czero<T>(), a1 = czero<T>(), a2 = czero<T>(), a3 = czero<T>();
+        for (int n = 0; n < nb; ++n) {
+          long long row = (((long long)side * nk + k) * nb + n) * 2;
+          cx<T> u0 = ur[row * nr + r], u1 = ur[(row + 1) * nr + r];
+          cx<T> x0 = xr[row * nr + r], x1 = xr[(row + 1) * nr + r];
+          cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
+          cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
+          a0 = cadd<T>(a0, cadd<T>(p00, p11));
+          a1 = cadd<T>(a1, cadd<T>(p01, p10));
+          cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
+          a2 = cadd<T>(a2, mk<T>(-d.y, d.x));
+          a3 = cadd<T>(a3, csub<T>(p00, p11));
+        }
+        T w = wk[k];
+        acc[0] = cadd<T>(acc[0], cscale<T>(a0, w));
+        acc[1] = cadd<T>(acc[1], cscale<T>(a1, w * t));
+        acc[2] = cadd<T>(acc[2], cscale<T>(a2, w * t));
+        acc[3] = cadd<T>(acc[3], cscale<T>(a3, w * t));
+      }
+    }
+    for (int a = 0; a < 4; ++a) rho[a * nr + r] = acc[a];
+  }
+}
+
+// --------------------------------------------------------- Hartree + ALSDA
+template <class T>
+__global__ void copy_scale_kernel(const cx<T> *__restrict__ a, cx<T> *__restrict__ b,
+                                  const T *__restrict__ fac, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = fac ? cscale<T>(a[i], fac[i]) : a[i];
+}
+
+template <class T>
+__global__ void scale_inplace_kernel(cx<T> *__restrict__ a, const T *__restrict__ fac,
+                                     long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] = cscale<T>(a[i], fac[i]);
+}
+
+// v_a = delta_a0 vH + sum_b f_ab rho_b ; f packed 00,01,02,03,11,12,13,22,23,33
+template <class T>
+__global__ void potential_kernel(const cx<T> *__restrict__ rho, const cx<T> *__restrict__ vh,
+                                 const T *__restrict__ f, cx<T> *__restrict__ v, long long nr,
+                                 int use_h, int use_xc) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+       r += (long long)gridDim.x * blockDim.x) {
+    cx<T> out[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+    if (use_xc) {
+      cx<T> p[4];
+      for (int a = 0; a < 4; ++a) p[a] = rho[a * nr + r];
+      T fm[4][4];
+      int q = 0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = a; b < 4; ++b) {
+          T val = f[q++ * nr + r];
+          fm[a][b] = val;
+          fm[b][a] = val;
+        }
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          out[a].x += fm[a][b] * p[b].x;
+          out[a].y += fm[a][b] * p[b].y;
+        }
+    }
+    if (use_h) out[0] = cadd<T>(out[0], vh[r]);
+    for (int a = 0; a < 4; ++a) v[a * nr + r] = out[a];
+  }
+}
+
+// -------------------------------------------------------- products (a6)
+// t = [v_loc + s B.sigma] x + W^s U, in place over x(r); W^s = v0 + s v.sigma.
+template <class T>
+__global__ void product_kernel(cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
+                               const T *__restrict__ vloc, const T *__restrict__ bf,
+                               const cx<T> *__restrict__ v, int nk, int nb, long long nr,
+                               long long nbs) {
+  long long bs = blockIdx.y + (long long)gridDim.y * blockIdx.z;  // band-side (side,k,n)
+  if (bs >= nbs) return;
+  int side = (int)(bs / ((long long)nk * nb));
+  T s = side == 0 ? T(1) : T(-1);
+  long long row = bs * 2;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+       r += (long long)gridDim.x * blockDim.x) {
+    T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
+    cx<T> v0 = v[r], v1 = v[nr + r], v2 = v[2 * nr + r], v3 = v[3 * nr + r];
+    cx<T> x0 = xr[row * nr + r], x1 = xr[(row + 1) * nr + r];
+    cx<T> u0 = ur[row * nr + r], u1 = ur[(row + 1) * nr + r];
+    // ground local 2x2: [[vl + s bz, s(bx - i by)], [s(bx + i by), vl - s bz]]
+    cx<T> h01 = mk<T>(s * bx, -s * by), h10 = mk<T>(s * bx, s * by);
+    cx<T> t0 = cscale<T>(x0, vl + s * bz);
+    cfma<T>(t0, h01, x1);
+    cx<T> t1 = cscale<T>(x1, vl - s * bz);
+    cfma<T>(t1, h10, x0);
+    // W^s: [[v0 + s v3, s(v1 - i v2)], [s(v1 + i v2), v0 - s v3]]
+    cx<T> w00 = mk<T>(v0.x + s * v3.x, v0.y + s * v3.y);
+    cx<T> w11 = mk<T>(v0.x - s * v3.x, v0.y - s * v3.y);
+    cx<T> w01 = mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x));
+    cx<T> w10 = mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x));
+    cfma<T>(t0, w00, u0);
+    cfma<T>(t0, w01, u1);
+    cfma<T>(t1, w10, u0);
+    cfma<T>(t1, w11, u1);
+    xr[row * nr + r] = t0;
+    xr[(row + 1) * nr + r] = t1;
+  }
+}
+
+// ------------------------------------------------------------------ GEMMs
+// Split-K reduction GEMM: part[z][b][m][n] = sum_{k in split z} conj(A[bA][m][k]) B[b][n][k].
+constexpr int TM = 32, TN = 32, KC = 16;
+template <class T>
+__global__ void __launch_bounds__(256)
+    gemm_tn_kernel(const cx<T> *__restrict__ A, long long lda, long long sA, int amod,
+                   const cx<T> *__restrict__ B, long long ldb, long long sB,
+                   cx<T> *__restrict__ part, int M, int N, long long K, int batch, int nsplit) {
+  __shared__ cx<T> As[TM][KC + 1];
+  __shared__ cx<T> Bs[TN][KC + 1];
+  int z = blockIdx.z;
+  int b = z % batch;
+  int sp = z / batch;
+  int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  long long kchunk = (K + nsplit - 1) / nsplit;
+  long long kb = sp * kchunk, ke = kb + kchunk < K ? kb + kchunk : K;
+  const cx<T> *Ab = A + (long long)(b % amod) * sA;
+  const cx<T> *Bb = B + (long long)b * sB;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<T> acc[2][2] = {{czero<T>(), czero<T>()}, {czero<T>(), czero<T>()}};
+  for (long long k0 = kb; k0 < ke; k0 += KC) {
+    for (int e = threadIdx.x; e < TM * KC; e += blockDim.x) {
+      int rr = e / KC, kk = e % KC;
+      long long kg = k0 + kk;
+      cx<T> av = czero<T>(), bv = czero<T>();
+      if (kg < ke) {
+        if (m0 + rr < M) av = Ab[(long long)(m0 + rr) * lda + kg];
+        if (n0 + rr < N) bv = Bb[(long long)(n0 + rr) * ldb + kg];
+      }
+      As[rr][kk] = av;
+      Bs[rr][kk] = bv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      cx<T> a0 = As[ty][kk], a1 = As[ty + 16][kk];
+      cx<T> b0 = Bs[tx][kk], b1 = Bs[tx + 16][kk];
+      cfmac<T>(acc[0][0], a0, b0);
+      cfmac<T>(acc[0][1], a0, b1);
+      cfmac<T>(acc[1][0], a1, b0);
+      cfmac<T>(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < M && n < N)
+        part[(((long long)sp * batch + b) * M + m) * N + n] = acc[i][j];
+    }
+}
+
+// C[b*sC + m*ldcm + n*ldcn] = sum_z part[z][b][m][n] (fixed order)
+template <class T>
+__global__ void split_reduce_kernel(const cx<T> *__restrict__ part, cx<T> *__restrict__ C,
+                                    int M, int N, int batch, int nsplit, long long sC,
+                                    long long ldcm, long long ldcn) {
+  long long total = (long long)batch * M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    cx<T> s = czero<T>();
+    for (int z = 0; z < nsplit; ++z) s = cadd<T>(s, part[(long long)z * total + i]);
+    long long b = i / ((long long)M * N);
+    long long rem = i - b * M * N;
+    long long m = rem / N, n = rem - m * N;
+    C[b * sC + m * ldcm + n * ldcn] = s;
+  }
+}
+
+// Out[b][row][col] = sgn_b (In[b][row][col] + alpha sum_k A(b,row,k) B[b % bmod][k][col])
+constexpr int NN_ROWS = 8, NN_COLS = 128, NN_KMAX = 256;
+template <class T>
+__global__ void __launch_bounds__(NN_COLS)
+    gemm_nn_kernel(const cx<T> *__restrict__ A, long long sA, long long sar, long long sak,
+                   const cx<T> *__restrict__ B, long long ldb, long long sB, int bmod,
+                   const cx<T> *In, cx<T> *Out, long long ldo, long long sO, int rows,
+                   long long ncol, int K, T alpha, int neg_from) {
+  __shared__ cx<T> As[NN_ROWS][NN_KMAX];
+  int b = blockIdx.z;
+  int r0 = blockIdx.y * NN_ROWS;
+  const cx<T> *Ab = A + (long long)b * sA;
+  for (int e = threadIdx.x; e < NN_ROWS * K; e += blockDim.x) {
+    int rr = e / K, kk = e % K;
+    As[rr][kk] = (r0 + rr < rows) ? Ab[(long long)(r0 + rr) * sar + (long long)kk * sak]
+                                  : czero<T>();
+  }
+  __syncthreads();
+  long long col = (long long)blockIdx.x * NN_COLS + threadIdx.x;
+  if (col >= ncol) return;
+  const cx<T> *Bb = B + (long long)(b % bmod) * sB;
+  cx<T> acc[NN_ROWS];
+#pragma unroll
+  for (int r = 0; r < NN_ROWS; ++r) acc[r] = czero<T>();
+  for (int kk = 0; kk < K; ++kk) {
+    cx<T> bv = Bb[(long long)kk * ldb + col];
+#pragma unroll
+    for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r][kk], bv);
+  }
+  T sg = b >= neg_from ? T(-1) : T(1);
+#pragma unroll
+  for (int r = 0; r < NN_ROWS; ++r) {
+    if (r0 + r >= rows) break;
+    long long o = (long long)b * sO + (long long)(r0 + r) * ldo + col;
+    cx<T> iv = In[o];
+    Out[o] = mk<T>(sg * (iv.x + alpha * acc[r].x), sg * (iv.y + alpha * acc[r].y));
+  }
+}
+
+// dmix[b][(n,s)][i] = sum_{j,t} D[2i+s][2j+t] proj[b][j][(n,t)]
+template <class T>
+__global__ void dmix_kernel(const cx<T> *__restrict__ proj, const cx<T> *__restrict__ dnl,
+                            cx<T> *__restrict__ dmix, int nproj, int nb, int batch) {
+  long long total = (long long)batch * nb * 2 * nproj;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e % nproj);
+    long long rest = e / nproj;
+    int s = (int)(rest % 2);
+    rest /= 2;
+    int n = (int)(rest % nb);
+    long long b = rest / nb;
+    const cx<T> *pb = proj + b * (long long)nproj * 2 * nb;
+    const cx<T> *drow = dnl + (long long)(2 * i + s) * 2 * nproj;
+    cx<T> acc = czero<T>();
+    for (int j = 0; j < nproj; ++j)
+      for (int t = 0; t < 2; ++t) cfma<T>(acc, drow[2 * j + t], pb[(long long)j * 2 * nb + 2 * n + t]);
+    dmix[e] = acc;
+  }
+}
+
+template <class T>
+void gemm_tn(Context &ctx, DevBuf &partbuf, const cx<T> *A, long long lda, long long sA, int amod,
+             const cx<T> *B, long long ldb, long long sB, cx<T> *C, long long sC, long long ldcm,
+             long long ldcn, int M, int N, long long K, int batch) {
+  int nsplit = (int)((K + 1023) / 1024);
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > 32) nsplit = 32;
+  size_t need = (size_t)nsplit * batch * M * N * sizeof(cx<T>);
+  TDLZ_REQUIRE(need <= partbuf.bytes, TDLZ_ERR_STATE, "split-K scratch too small");
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, (unsigned)(batch * nsplit));
+  gemm_tn_kernel<T><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB,
+                                                   partbuf.template as<cx<T>>(), M, N, K, batch,
+                                                   nsplit);
+  TDLZ_LAUNCH_CHECK();
+  long long tot = (long long)batch * M * N;
+  split_reduce_kernel<T><<<blocks_for(tot), kThreads, 0, ctx.stream>>>(
+      partbuf.template as<cx<T>>(), C, M, N, batch, nsplit, sC, ldcm, ldcn);
+  TDLZ_LAUNCH_CHECK();
+}
+
+template <class T>
+void gemm_nn(Context &ctx, const cx<T> *A, long long sA, long long sar, long long sak,
+             const cx<T> *B, long long ldb, long long sB, int bmod, const cx<T> *In, cx<T> *Out,
+             long long ldo, long long sO, int rows, long long ncol, int K, T alpha, int batch,
+             int neg_from) {
+  TDLZ_REQUIRE(K <= NN_KMAX, TDLZ_ERR_ARG, "contraction length above 256 (nocc or nproj)");
+  dim3 grid((unsigned)((ncol + NN_COLS - 1) / NN_COLS), (rows + NN_ROWS - 1) / NN_ROWS, batch);
+  gemm_nn_kernel<T><<<grid, NN_COLS, 0, ctx.stream>>>(A, sA, sar, sak, B, ldb, sB, bmod, In, Out,
+                                                     ldo, sO, rows, ncol, K, alpha, neg_from);
+  TDLZ_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------- precision conversion
+template <class S, class D>
+__global__ void convert_kernel(const S *__restrict__ a, D *__restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (D)a[i];
+}
+
+template <class T>
+void convert_buf(Context &ctx, const DevBuf &src, DevBuf &dst) {
+  long long n = src.bytes / sizeof(double);
+  dst.alloc(n * sizeof(T));
+  convert_kernel<double, T><<<blocks_for(n), kThreads, 0, ctx.stream>>>(
+      src.as<double>(), dst.as<T>(), n);
+  TDLZ_LAUNCH_CHECK();
+}
+
+// ----------------------------------------------------- XC kernel table
+// Spin-polarised Slater exchange e = -(3/4)(6/pi)^{1/3}(n_u^{4/3} + n_d^{4/3}),
+// n_u/d = (n +- |m|)/2 floored at 1e-4, f = 0 for n < 1e-10; second
+// derivatives w.r.t. (n, m) through |m| (Eqs. v_XC_q, b_XC_q).
+__global__ void fxc_kernel(const double *__restrict__ n0, const double *__restrict__ m0,
+                           double *__restrict__ f, long long nr) {
+  const double c6 = cbrt(6.0 / 3.14159265358979323846);
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+       r += (long long)gridDim.x * blockDim.x) {
+    double fm[4][4] = {{0}};
+    double n = n0[r];
+    if (n >= 1e-10) {
+      double mx = m0[r], my = m0[nr + r], mz = m0[2 * nr + r];
+      double ma = sqrt(mx * mx + my * my + mz * mz);
+      double nu = fmax(0.5 * (n + ma), 1e-4), nd = fmax(0.5 * (n - ma), 1e-4);
+      double fu = -(c6 / 3.0) / cbrt(nu * nu), fd = -(c6 / 3.0) / cbrt(nd * nd);
+      double h[3], tr;
+      if (ma < 1e-12 * n) {
+        h[0] = 0.0;
+        h[1] = 0.0;
+        h[2] = 1.0;
+        double nh = fmax(0.5 * n, 1e-4);
+        tr = 0.5 * (-(c6 / 3.0) / cbrt(nh * nh));
+      } else {
+        h[0] = mx / ma;
+        h[1] = my / ma;
+        h[2] = mz / ma;
+        double vu = -cbrt(6.0 * nu / 3.14159265358979323846);
+        double vd = -cbrt(6.0 * nd / 3.14159265358979323846);
+        tr = (vu - vd) / (2.0 * ma);
+      }
+      double sp = 0.25 * (fu + fd), sm = 0.25 * (fu - fd);
+      fm[0][0] = sp;
+      for (int i = 0; i < 3; ++i) {
+        fm[0][i + 1] = fm[i + 1][0] = sm * h[i];
+        for (int j = 0; j < 3; ++j)
+          fm[i + 1][j + 1] = sp * h[i] * h[j] + tr * ((i == j ? 1.0 : 0.0) - h[i] * h[j]);
+      }
+    }
+    int q = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a; b < 4; ++b) f[(long long)(q++) * nr + r] = fm[a][b];
+  }
+}
+
+// ---------------------------------------------------------- start vectors
+// v[b][n][s][g] = sum_t sigma^mu[s][t] c_k[b][n][t][map[g]]  (G of the k+q sphere
+// found in the k sphere; 0 otherwise).  ysign multiplies the Y side.
+template <class T>
+__global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restrict__ map, int mu,
+                               cx<T> *__restrict__ out, int nk, int nb, int npwx, T ysign) {
+  long long total = 2LL * nk * nb * npwx;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int g = (int)(e % npwx);
+    long long band = e / npwx;  // (side, k, n)
+    int k = (int)((band / nb) % nk);
+    int side = (int)(band / ((long long)nk * nb));
+    int mg = map[(long long)k * npwx + g];
+    cx<T> c0 = czero<T>(), c1 = czero<T>();
+    if (mg >= 0) {
+      c0 = ck[(band * 2) * npwx + mg];
+      c1 = ck[(band * 2 + 1) * npwx + mg];
+    }
+    cx<T> o0, o1;
+    if (mu == 0) {  // sigma_x
+      o0 = c1;
+      o1 = c0;
+    } else if (mu == 1) {  // sigma_y: (-i c1, i c0)
+      o0 = mk<T>(c1.y, -c1.x);
+      o1 = mk<T>(-c0.y, c0.x);
+    } else {  // sigma_z
+      o0 = c0;
+      o1 = mk<T>(-c1.x, -c1.y);
+    }
+    T sg = side == 1 ? ysign : T(1);
+    out[(band * 2) * npwx + g] = cscale<T>(o0, sg);
+    out[(band * 2 + 1) * npwx + g] = cscale<T>(o1, sg);
+  }
+}
+
+
+template <class T>
+void alloc_workspace(QSlot &s) {
+  Workspace<T> &w = slot_ws<T>(s);
+  if (w.ready) return;
+  size_t c = sizeof(cx<T>);
+  w.xr.alloc((size_t)s.rows() * s.nr * c);
+  w.rho.alloc(4 * (size_t)s.nr * c);
+  w.vpot.alloc(4 * (size_t)s.nr * c);
+  w.hgrid.alloc((size_t)s.nr * c);
+  w.h.alloc((size_t)s.br_elems() * c);
+  w.xin.alloc((size_t)s.br_elems() * c);
+  int batch = 2 * s.nk;
+  w.proj.alloc((size_t)batch * s.nproj * 2 * s.nb * c + c);
+  w.dmix.alloc((size_t)batch * s.nproj * 2 * s.nb * c + c);
+  w.ovl.alloc((size_t)batch * s.nb * s.nb * c);
+  size_t p1 = (size_t)32 * batch * std::max(s.nproj, 1) * 2 * s.nb;
+  size_t p2 = (size_t)32 * batch * s.nb * s.nb;
+  w.part.alloc(std::max(p1, p2) * c);
+  w.ready = true;
+}
+
+}  // namespace
+
+// ===================================================================== load
+void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
+  // ---- validation (host; nothing launched on failure)
+  TDLZ_REQUIRE(gs != nullptr, TDLZ_ERR_ARG, "ground state is NULL");
+  TDLZ_REQUIRE(gs->nk >= 1 && gs->nocc >= 1 && gs->npwx >= 1 && gs->nproj >= 0, TDLZ_ERR_ARG,
+               "nk, nocc, npwx must be >= 1 and nproj >= 0");
+  TDLZ_REQUIRE(gs->nocc <= 256 && gs->nproj <= 256, TDLZ_ERR_ARG, "nocc and nproj must be <= 256");
+  for (int d = 0; d < 3; ++d)
+    TDLZ_REQUIRE(fft_length_supported(gs->fft[d]), TDLZ_ERR_ARG,
+                 "FFT lengths must be products of 2, 3, 5 and <= 512");
+  double qn = std::sqrt(gs->q[0] * gs->q[0] + gs->q[1] * gs->q[1] + gs->q[2] * gs->q[2]);
+  TDLZ_REQUIRE(qn > 1e-8, TDLZ_ERR_ARG, "|q| must exceed 1e-8 (q = 0 is a separate limit)");
+  TDLZ_REQUIRE(gs->ecutwfc > 0, TDLZ_ERR_ARG, "ecutwfc must be positive");
+  const char *ptr_names[] = {"kpts", "wk", "npw_k", "npw_kq", "miller_k", "miller_kq", "evals",
+                             "coeff_k", "coeff_kq", "vloc", "bfield", "n0", "m0", "dnl"};
+  const void *ptrs[] = {gs->kpts, gs->wk, gs->npw_k, gs->npw_kq, gs->miller_k, gs->miller_kq,
+                        gs->evals, gs->coeff_k, gs->coeff_kq, gs->vloc, gs->bfield, gs->n0,
+                        gs->m0, gs->dnl};
+  for (int i = 0; i < 14; ++i)
+    TDLZ_REQUIRE(ptrs[i] != nullptr || (i == 13 && gs->nproj == 0), TDLZ_ERR_ARG,
+                 std::string("NULL array: ") + ptr_names[i]);
+  TDLZ_REQUIRE(gs->nproj == 0 || gs->beta_kq != nullptr, TDLZ_ERR_ARG, "NULL array: beta_kq");
+  const int nk = gs->nk, nb = gs->nocc, npwx = gs->npwx, np_ = gs->nproj;
+  const long long nr = (long long)gs->fft[0] * gs->fft[1] * gs->fft[2];
+  for (int k = 0; k < nk; ++k) {
+    TDLZ_REQUIRE(gs->npw_k[k] >= 1 && gs->npw_k[k] <= npwx && gs->npw_kq[k] >= 1 &&
+                     gs->npw_kq[k] <= npwx,
+                 TDLZ_ERR_ARG, "npw_k / npw_kq out of range [1, npwx]");
+    TDLZ_REQUIRE(std::isfinite(gs->wk[k]) && gs->wk[k] > 0, TDLZ_ERR_ARG, "k weights must be > 0");
+  }
+  auto finite_all = [](const double *p, long long n) {
+    for (long long i = 0; i < n; ++i)
+      if (!std::isfinite(p[i])) return false;
+    return true;
+  };
+  long long brd = 2LL * nk * nb * 2 * npwx * 2;
+  TDLZ_REQUIRE(finite_all(gs->coeff_k, brd) && finite_all(gs->coeff_kq, brd) &&
+                   finite_all(gs->evals, 2LL * nk * nb) && finite_all(gs->vloc, nr) &&
+                   finite_all(gs->bfield, 3 * nr) && finite_all(gs->n0, nr) &&
+                   finite_all(gs->m0, 3 * nr) && finite_all(gs->kpts, 3LL * nk),
+               TDLZ_ERR_ARG, "non-finite value in the ground state");
+  if (np_ > 0) {
+    TDLZ_REQUIRE(finite_all(gs->dnl, 4LL * np_ * np_ * 2) &&
+                     finite_all(gs->beta_kq, (long long)nk * np_ * npwx * 2),
+                 TDLZ_ERR_ARG, "non-finite projector data");
+    int nd = 2 * np_;
+    double dmax = 0, herr = 0;
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < nd; ++j) {
+        const double *a = gs->dnl + 2 * ((long long)i * nd + j);
+        const double *b = gs->dnl + 2 * ((long long)j * nd + i);
+        dmax = std::max(dmax, std::hypot(a[0], a[1]));
+        herr = std::max(herr, std::hypot(a[0] - b[0], a[1] + b[1]));
+      }
+    TDLZ_REQUIRE(herr <= 1e-12 * std::max(dmax, 1e-300), TDLZ_ERR_ARG,
+                 "dnl is not Hermitian");
+  }
+  // grid indices + sphere checks
+  std::vector<int> idx_k((size_t)nk * npwx, -1), idx_kq((size_t)nk * npwx, -1),
+      map((size_t)nk * npwx, -1);
+  auto gidx = [&](const int *m, int &out) {
+    long long id = 0;
+    for (int d = 0; d < 3; ++d) {
+      int n = gs->fft[d];
+      if (m[d] < -(n / 2) || m[d] > (n - 1) / 2) return false;
+      id = id * n + ((m[d] % n) + n) % n;
+    }
+    out = (int)id;
+    return true;
+  };
+  for (int k = 0; k < nk; ++k) {
+    std::unordered_map<int, int> where;
+    for (int g = 0; g < gs->npw_k[k]; ++g) {
+      int id;
+      TDLZ_REQUIRE(gidx(gs->miller_k + 3 * ((long long)k * npwx + g), id), TDLZ_ERR_ARG,
+                   "k sphere does not fit the FFT box");
+      TDLZ_REQUIRE(where.emplace(id, g).second, TDLZ_ERR_ARG, "duplicate Miller index (k)");
+      idx_k[(size_t)k * npwx + g] = id;
+    }
+    std::unordered_map<int, int> seen;
+    for (int g = 0; g < gs->npw_kq[k]; ++g) {
+      int id;
+      TDLZ_REQUIRE(gidx(gs->miller_kq + 3 * ((long long)k * npwx + g), id), TDLZ_ERR_ARG,
+                   "k+q sphere does not fit the FFT box");
+      TDLZ_REQUIRE(seen.emplace(id, g).second, TDLZ_ERR_ARG, "duplicate Miller index (k+q)");
+      idx_kq[(size_t)k * npwx + g] = id;
+      auto it = where.find(id);
+      map[(size_t)k * npwx + g] = it == where.end() ? -1 : it->second;
+    }
+  }
+  // ---- host-side geometry
+  s.nk = nk;
+  s.nb = nb;
+  s.npwx = npwx;
+  s.nproj = np_;
+  s.kernel_mask = gs->kernel_mask;
+  for (int d = 0; d < 3; ++d) s.fft[d] = gs->fft[d];
+  s.nr = nr;
+  for (int d = 0; d < 3; ++d) s.q[d] = gs->q[d];
+  const double *A = gs->lattice;
+  double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+               A[2] * (A[3] * A[7] - A[4] * A[6]);
+  TDLZ_REQUIRE(std::fabs(det) > 1e-12, TDLZ_ERR_ARG, "singular lattice");
+  s.omega = std::fabs(det);
+  // reciprocal rows b_j = 2 pi (A^{-1})^T  rows
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = -(A[1] * A[8] - A[2] * A[7]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = -(A[3] * A[8] - A[5] * A[6]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = -(A[0] * A[5] - A[2] * A[3]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = -(A[0] * A[7] - A[1] * A[6]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  double bv[3][3];  // bv[j][c] = 2 pi inv[c][j]
+  for (int j = 0; j < 3; ++j)
+    for (int c = 0; c < 3; ++c) bv[j][c] = 2.0 * 3.14159265358979323846 * inv[c * 3 + j];
+  s.npw_k.assign(gs->npw_k, gs->npw_k + nk);
+  s.npw_kq.assign(gs->npw_kq, gs->npw_kq + nk);
+  s.wk.assign(gs->wk, gs->wk + nk);
+  std::vector<double> kin((size_t)nk * npwx, 0.0);
+  for (int k = 0; k < nk; ++k)
+    for (int g = 0; g < gs->npw_kq[k]; ++g) {
+      const int *m = gs->miller_kq + 3 * ((long long)k * npwx + g);
+      double v[3];
+      for (int c = 0; c < 3; ++c)
+        v[c] = gs->kpts[3 * k + c] + gs->q[c] + m[0] * bv[0][c] + m[1] * bv[1][c] + m[2] * bv[2][c];
+      kin[(size_t)k * npwx + g] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+  // Hartree factor on the grid: 4 pi/|q+G|^2 / Nr where |q+G|^2/2 <= 4 ecut
+  std::vector<double> vh(nr, 0.0);
+  {
+    long long id = 0;
+    for (int i1 = 0; i1 < gs->fft[0]; ++i1)
+      for (int i2 = 0; i2 < gs->fft[1]; ++i2)
+        for (int i3 = 0; i3 < gs->fft[2]; ++i3, ++id) {
+          int m[3] = {i1, i2, i3};
+          for (int d = 0; d < 3; ++d)
+            if (m[d] >= (gs->fft[d] + 1) / 2) m[d] -= gs->fft[d];
+          double v[3];
+          for (int c = 0; c < 3; ++c)
+            v[c] = gs->q[c] + m[0] * bv[0][c] + m[1] * bv[1][c] + m[2] * bv[2][c];
+          double g2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          if (0.5 * g2 <= 4.0 * gs->ecutwfc) vh[id] = 4.0 * 3.14159265358979323846 / g2 / nr;
+        }
+  }
+  // ---- device upload (FP64 master copies)
+  cudaStream_t st = ctx.stream;
+  auto up = [&](DevBuf &b, const void *src, size_t bytes) {
+    b.alloc(bytes);
+    TDLZ_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+  };
+  s.plan.init(gs->fft);
+  up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
+  up(s.idx_kq, idx_kq.data(), idx_kq.size() * sizeof(int));
+  up(s.map_kq_k, map.data(), map.size() * sizeof(int));
+  up(s.npwkq_d, gs->npw_kq, nk * sizeof(int));
+  SlotData<double> &d = s.d64;
+  size_t brb = (size_t)s.br_elems() * sizeof(double2);
+  up(d.ukq, gs->coeff_kq, brb);
+  up(s.coeff_k, gs->coeff_k, brb);
+  if (np_ > 0) {
+    up(d.beta, gs->beta_kq, (size_t)nk * np_ * npwx * sizeof(double2));
+    up(d.dnl, gs->dnl, (size_t)4 * np_ * np_ * sizeof(double2));
+  }
+  up(d.kin, kin.data(), kin.size() * sizeof(double));
+  up(d.evals, gs->evals, (size_t)2 * nk * nb * sizeof(double));
+  up(d.vloc, gs->vloc, nr * sizeof(double));
+  up(d.bfield, gs->bfield, 3 * nr * sizeof(double));
+  up(d.vhfac, vh.data(), nr * sizeof(double));
+  up(d.wk, gs->wk, nk * sizeof(double));
+  DevBuf n0d, m0d;
+  up(n0d, gs->n0, nr * sizeof(double));
+  up(m0d, gs->m0, 3 * nr * sizeof(double));
+  d.fxc.alloc(10 * nr * sizeof(double));
+  fxc_kernel<<<blocks_for(nr), kThreads, 0, st>>>(n0d.as<double>(), m0d.as<double>(),
+                                                  d.fxc.as<double>(), nr);
+  TDLZ_LAUNCH_CHECK();
+  // real-space occupied orbitals U(r) = Omega^{-1/2} sum_G c exp(iG.r)
+  d.ur.alloc((size_t)s.rows() * nr * sizeof(double2));
+  TDLZ_CUDA_TRY(cudaMemsetAsync(d.ur.p, 0, d.ur.bytes, st));
+  scatter_rows_kernel<double><<<row_grid(s.rows(), npwx), kThreads, 0, st>>>(
+      s.coeff_k.as<double2>(), d.ur.as<double2>(), s.idx_k.as<int>(), nk, nb, npwx, nr,
+      1.0 / std::sqrt(s.omega), s.rows());
+  TDLZ_LAUNCH_CHECK();
+  fft3d<double>(s.plan, d.ur.as<double2>(), s.rows(), +1, st);
+  // u^lambda = J sigma^lambda U on the k+q sphere (unprojected)
+  d.uvec.alloc(3 * brb);
+  for (int l = 0; l < 3; ++l) {
+    sigma_u_kernel<double><<<blocks_for(2LL * nk * nb * npwx), kThreads, 0, st>>>(
+        s.coeff_k.as<double2>(), s.map_kq_k.as<int>(), l, d.uvec.as<double2>() + l * s.br_elems(),
+        nk, nb, npwx, -1.0);
+    TDLZ_LAUNCH_CHECK();
+  }
+  d.ready = true;
+  TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+template <class T>
+void ensure_precision(Context &ctx, QSlot &s) {
+  if constexpr (sizeof(T) == 4) {
+    SlotData<float> &f = s.d32;
+    if (!f.ready) {
+      SlotData<double> &d = s.d64;
+      convert_buf<float>(ctx, d.ukq, f.ukq);
+      convert_buf<float>(ctx, d.ur, f.ur);
+      if (s.nproj > 0) {
+        convert_buf<float>(ctx, d.beta, f.beta);
+        convert_buf<float>(ctx, d.dnl, f.dnl);
+      }
+      convert_buf<float>(ctx, d.kin, f.kin);
+      convert_buf<float>(ctx, d.evals, f.evals);
+      convert_buf<float>(ctx, d.vloc, f.vloc);
+      convert_buf<float>(ctx, d.bfield, f.bfield);
+      convert_buf<float>(ctx, d.fxc, f.fxc);
+      convert_buf<float>(ctx, d.vhfac, f.vhfac);
+      convert_buf<float>(ctx, d.wk, f.wk);
+      convert_buf<float>(ctx, d.uvec, f.uvec);
+      f.ready = true;
+    }
+  }
+  alloc_workspace<T>(s);
+}
+
+// ==================================================================== apply
+template <class T>
+void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool adjoint) {
+  ensure_precision<T>(ctx, s);
+  SlotData<T> &d = slot_data<T>(s);
+  Workspace<T> &w = slot_ws<T>(s);
+  cudaStream_t st = ctx.stream;
+  Profiler &pf = ctx.prof;
+  const int nk = s.nk, nb = s.nb, npwx = s.npwx, np_ = s.nproj;
+  const long long nr = s.nr, rows = s.rows(), nbs = rows / 2;
+  const int batch = 2 * nk;
+  // algorithmic traffic / work per stage (see the design doc for the definitions)
+  const double c = sizeof(cx<T>), re = sizeof(T);
+  const double V = (double)s.br_elems(), G = (double)rows * nr;
+  const double fft_flops = (double)rows * 5.0 * nr * std::log2((double)nr);
+  if (adjoint) {  // L^H x = J L J x
+    ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
+    jflip_copy<T>(ctx, s, x, w.xin.template as<cx<T>>());
+    x = w.xin.template as<cx<T>>();
+  }
+  cx<T> *xr = w.xr.template as<cx<T>>();
+  // 1. sphere -> grid -> real space
+  {
+    ProfScope ps(pf, st, ST_SCATTER, V * c + G * c, 0);
+    TDLZ_CUDA_TRY(cudaMemsetAsync(xr, 0, w.xr.bytes, st));
+    scatter_rows_kernel<T><<<row_grid(rows, npwx), kThreads, 0, st>>>(
+        x, xr, s.idx_kq.as<int>(), nk, nb, npwx, nr, (T)(1.0 / std::sqrt(s.omega)), rows);
+    TDLZ_LAUNCH_CHECK();
+  }
+  {
+    ProfScope ps(pf, st, ST_FFT_INV, 3 * 2 * G * c, fft_flops);
+    fft3d<T>(s.plan, xr, rows, +1, st);
+  }
+  // 2-4. densities and HXC potential
+  cx<T> *rho = w.rho.template as<cx<T>>();
+  cx<T> *vp = w.vpot.template as<cx<T>>();
+  cx<T> *hg = w.hgrid.template as<cx<T>>();
+  const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
+  if (use_h || use_xc) {
+    {
+      ProfScope ps(pf, st, ST_DENSITY, 2 * G * c + 4 * nr * c, (double)nbs * nr * 40.0);
+      density_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(d.ur.template as<cx<T>>(), xr,
+                                                            d.wk.template as<T>(), rho, nk, nb, nr);
+      TDLZ_LAUNCH_CHECK();
+    }
+    if (use_h) {
+      ProfScope ps(pf, st, ST_HARTREE, 8 * nr * c, 2 * 5.0 * nr * std::log2((double)nr));
+      copy_scale_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(rho, hg, nullptr, nr);
+      TDLZ_LAUNCH_CHECK();
+      fft3d<T>(s.plan, hg, 1, -1, st);
+      scale_inplace_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(hg, d.vhfac.template as<T>(),
+                                                                  nr);
+      TDLZ_LAUNCH_CHECK();
+      fft3d<T>(s.plan, hg, 1, +1, st);
+    }
+    ProfScope ps(pf, st, ST_POTENTIAL, 9 * nr * c + 10 * nr * re, 16.0 * 4 * nr);
+    potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(rho, hg, d.fxc.template as<T>(), vp,
+                                                            nr, use_h ? 1 : 0, use_xc ? 1 : 0);
+    TDLZ_LAUNCH_CHECK();
+  } else {
+    TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
+  }
+  // 5. local products in place
+  {
+    ProfScope ps(pf, st, ST_PRODUCT, 3 * G * c + 4 * nr * (c + re), (double)nbs * nr * 64.0);
+    unsigned bx = blocks_for(nr);
+    if (bx > 64) bx = 64;
+    long long yz = nbs, z = 1;
+    while (yz > 65535) {
+      z *= 2;
+      yz = (nbs + z - 1) / z;
+    }
+    product_kernel<T><<<dim3(bx, (unsigned)yz, (unsigned)z), kThreads, 0, st>>>(
+        xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(), d.bfield.template as<T>(), vp, nk,
+        nb, nr, nbs);
+    TDLZ_LAUNCH_CHECK();
+  }
+  // 6. real space -> sphere, + (kin - e) x
+  {
+    ProfScope ps(pf, st, ST_FFT_FWD, 3 * 2 * G * c, fft_flops);
+    fft3d<T>(s.plan, xr, rows, -1, st);
+  }
+  cx<T> *h = w.h.template as<cx<T>>();
+  {
+    ProfScope ps(pf, st, ST_GATHER, 3 * V * c + V / 2 * re, 6.0 * V);
+    gather_rows_kernel<T><<<row_grid(rows, npwx), kThreads, 0, st>>>(
+        xr, x, h, s.idx_kq.as<int>(), d.kin.template as<T>(), d.evals.template as<T>(), nk, nb,
+        npwx, nr, (T)(std::sqrt(s.omega) / nr), rows);
+    TDLZ_LAUNCH_CHECK();
+  }
+  // 7. nonlocal pseudopotential
+  const long long bstride = (long long)nb * 2 * npwx;
+  if (np_ > 0) {
+    double bb = (double)nk * np_ * npwx * c;
+    ProfScope ps(pf, st, ST_VNL, 3 * V * c + 2 * bb,
+                 2 * 8.0 * batch * (double)np_ * 2 * nb * npwx);
+    cx<T> *proj = w.proj.template as<cx<T>>();
+    cx<T> *dm = w.dmix.template as<cx<T>>();
+    gemm_tn<T>(ctx, w.part, d.beta.template as<cx<T>>(), npwx, (long long)np_ * npwx, nk, x, npwx,
+               bstride, proj, (long long)np_ * 2 * nb, 2 * nb, 1, np_, 2 * nb, npwx, batch);
+    long long tot = (long long)batch * nb * 2 * np_;
+    dmix_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(proj, d.dnl.template as<cx<T>>(), dm,
+                                                        np_, nb, batch);
+    TDLZ_LAUNCH_CHECK();
+    gemm_nn<T>(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<cx<T>>(), npwx,
+               (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
+               batch);
+  }
+  // 8. P_c and the row sign
+  {
+    ProfScope ps(pf, st, ST_PC, 5 * V * c, 2 * 8.0 * batch * (double)nb * nb * 2 * npwx);
+    cx<T> *ov = w.ovl.template as<cx<T>>();
+    const cx<T> *ukq = d.ukq.template as<cx<T>>();
+    gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch, h, 2LL * npwx, bstride, ov,
+               (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
+    gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch, h, y,
+               2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk);
+  }
+  if (adjoint) {
+    ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
+    jflip_copy<T>(ctx, s, y, y);
+  }
+}
+
+// v^mu = (P sigma^mu U, P+ sigma^mu T U) on the k+q spheres (Sec. 2.5).
+template <class T>
+void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v) {
+  cudaStream_t st = ctx.stream;
+  const int nk = s.nk, nb = s.nb, npwx = s.npwx;
+  const int batch = 2 * nk;
+  const long long bstride = (long long)nb * 2 * npwx;
+  DevBuf tmpb, ovb, partb;
+  tmpb.alloc((size_t)s.br_elems() * sizeof(double2));
+  ovb.alloc((size_t)batch * nb * nb * sizeof(double2));
+  partb.alloc((size_t)32 * batch * nb * nb * sizeof(double2));
+  double2 *tmp = tmpb.as<double2>();
+  sigma_u_kernel<double><<<blocks_for(2LL * nk * nb * npwx), kThreads, 0, st>>>(
+      s.coeff_k.as<double2>(), s.map_kq_k.as<int>(), mu, tmp, nk, nb, npwx, 1.0);
+  TDLZ_LAUNCH_CHECK();
+  double2 *ov = ovb.as<double2>();
+  const double2 *ukq = s.d64.ukq.as<double2>();
+  gemm_tn<double>(ctx, partb, ukq, 2LL * npwx, bstride, batch, tmp, 2LL * npwx, bstride, ov,
+                  (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
+  if constexpr (sizeof(T) == 8) {
+    gemm_nn<double>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch, tmp, v,
+                    2LL * npwx, bstride, nb, 2LL * npwx, nb, -1.0, batch, batch);
+  } else {
+    gemm_nn<double>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch, tmp, tmp,
+                    2LL * npwx, bstride, nb, 2LL * npwx, nb, -1.0, batch, batch);
+    long long n = s.br_elems() * 2;
+    convert_kernel<double, float><<<blocks_for(n), kThreads, 0, st>>>(
+        reinterpret_cast<const double *>(tmp), reinterpret_cast<float *>(v), n);
+    TDLZ_LAUNCH_CHECK();
+  }
+  TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+template void ensure_precision<double>(Context &, QSlot &);
+template void ensure_precision<float>(Context &, QSlot &);
+template void apply_liouvillian<double>(Context &, QSlot &, const double2 *, double2 *, bool);
+template void apply_liouvillian<float>(Context &, QSlot &, const float2 *, float2 *, bool);
+template void start_vector<double>(Context &, QSlot &, int, double2 *);
+template void start_vector<float>(Context &, QSlot &, int, float2 *);
+
+}  // namespace tdlz

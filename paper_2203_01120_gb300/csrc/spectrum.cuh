@@ -1,0 +1,23 @@
+// Spectrum kernel arguments (device pointers).
+#pragma once
+
+#include "engine.cuh"
+
+namespace tdlz {
+
+struct SpecArgs {
+  int nchain, nomega, cap;
+  const int *steps;      // [nchain]
+  const double2 *alpha;  // [nchain][cap]
+  const double *beta;    // [nchain][cap]
+  const double2 *gamma;  // [nchain][cap]
+  const double2 *z;      // [nchain][3][cap]
+  const double *n0, *wk; // [nchain]
+  double start, step, eta;
+  double2 *scratch;      // [4][cap][nchain*nomega]
+  double2 *chi;          // [nchain][3][nomega]
+};
+
+void launch_spectrum(cudaStream_t st, const SpecArgs &a);
+
+}  // namespace tdlz

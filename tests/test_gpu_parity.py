@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated here, derived in the design doc):
+* one Liouvillian application, FP64: relative L2 error <= 1e-12;
+* one Liouvillian application, mixed (FP32 storage/arithmetic): <= 2e-5;
+* Lanczos coefficients, FP64, NH and positive-definite PH: <= 1e-9 relative to
+  the largest coefficient over 50 steps; J-metric PH over its first 12 steps on
+  the longitudinal chain at 1e-7: its alternating tiny beta amplify the 1e-15
+  differences of two correct FP64 codes by ~1e7 (the same spread appears between
+  the oracle's matrix-free and dense runs);
+* spectrum from identical coefficients: <= 1e-12 relative;
+* chi(omega) end to end at eta = 10 meV, FP64: <= 1e-8 relative.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from _cases import ground_state, liouvillian  # noqa: E402
+from synth import random_br_vector  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2203_01120_gb300 import Context, build
+    build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+_slots = {}
+
+
+def slot(ctx, name, mask=3, collinear=False):
+    key = (name, mask, collinear)
+    if key not in _slots:
+        _slots[key] = ctx.load_ground_state(ground_state(name, mask, collinear))
+    return _slots[key]
+
+
+def apply_gpu(torch, ctx, q, x, adjoint=False, mixed=False):
+    from paper_2203_01120_gb300 import TDLZ_FP64, TDLZ_MIXED
+    dt = torch.complex64 if mixed else torch.complex128
+    xt = torch.as_tensor(x, dtype=dt, device="cuda").contiguous()
+    yt = torch.zeros_like(xt)
+    ctx.apply_liouvillian(q, xt, yt, adjoint, TDLZ_MIXED if mixed else TDLZ_FP64)
+    ctx.synchronize()
+    return yt.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("name,mask", [("C0", 3), ("C0K", 0), ("C0K", 1), ("C0K", 2), ("C0K", 3),
+                                       ("C1", 3)])
+def test_apply_fp64(torch, ctx, name, mask):
+    q = slot(ctx, name, mask)
+    lv = liouvillian(name, mask)
+    x = random_br_vector(lv.gs, seed=7)
+    y = apply_gpu(torch, ctx, q, x)
+    ref = lv.apply(x)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err <= 1e-12, err
+    # padding stays zero
+    for k in range(lv.gs.nk):
+        assert not y[:, k, :, :, lv.gs.npw_kq[k]:].any()
+
+
+def test_apply_adjoint_fp64(torch, ctx):
+    q = slot(ctx, "C0K")
+    lv = liouvillian("C0K")
+    x = random_br_vector(lv.gs, seed=8)
+    y = apply_gpu(torch, ctx, q, x, adjoint=True)
+    ref = lv.apply_adjoint(x)
+    assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", ["C0K", "C1"])
+def test_apply_mixed(torch, ctx, name):
+    q = slot(ctx, name)
+    lv = liouvillian(name)
+    x = random_br_vector(lv.gs, seed=9)
+    y = apply_gpu(torch, ctx, q, x, mixed=True)
+    ref = lv.apply(x)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err <= 2e-5, err
+
+
+def test_apply_is_deterministic(torch, ctx):
+    q = slot(ctx, "C1")
+    lv = liouvillian("C1")
+    x = random_br_vector(lv.gs, seed=10)
+    a = apply_gpu(torch, ctx, q, x)
+    b = apply_gpu(torch, ctx, q, x)
+    assert np.array_equal(a, b)
+
+
+def _oracle_chain(name, mu, steps, flavor, mask=3):
+    from oracle.lanczos import run_chain
+    return run_chain(liouvillian(name, mask), mu, steps, flavor)
+
+
+@pytest.mark.parametrize("flavor,mu,steps,tol", [("nh", 0, 50, 1e-9), ("phm", 0, 50, 1e-9),
+                                                 ("nh", 2, 50, 1e-9), ("ph", 2, 12, 1e-7)])
+def test_lanczos_fp64(torch, ctx, flavor, mu, steps, tol):
+    q = slot(ctx, "C1")
+    got = ctx.lanczos_run([q], [mu], steps, flavor)
+    ref = _oracle_chain("C1", mu, steps, flavor)
+    assert got["status"][0] == 0 and got["steps_done"][0] == steps
+    assert abs(got["n0"][0] - ref.n0) <= 1e-12 * ref.n0
+    for key, r in (("alpha", ref.alpha), ("beta", ref.beta), ("gamma", ref.gamma)):
+        g = got[key][0]
+        assert np.max(np.abs(g - r)) <= tol * np.max(np.abs(r)), key
+    assert np.max(np.abs(got["z"][0] - ref.z)) <= tol * np.max(np.abs(ref.z))
+
+
+def test_spectrum_matches_oracle_on_same_coefficients(torch, ctx):
+    from oracle.lanczos import Coefficients
+    from oracle.spectrum import chi_banded, omega_grid_mev, HA_MEV
+    q = slot(ctx, "C1")
+    got = ctx.lanczos_run([q, q], [0, 2], 50, "nh")
+    chi = ctx.spectrum(got, 0.0, 400.0, 0.5, 10.0, units=1)
+    om = omega_grid_mev(0.0, 400.0, 0.5) / HA_MEV
+    for c in range(2):
+        co = Coefficients(got["alpha"][c], got["beta"][c], got["gamma"][c], got["z"][c],
+                          got["n0"][c], int(got["steps_done"][c]), "ok")
+        ref = chi_banded(co, om, 10.0 / HA_MEV, got["wk"][c])
+        assert chi.shape == (2, 3, len(om))
+        assert np.max(np.abs(chi[c] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("flavor", ["nh", "phm"])
+def test_chi_end_to_end_fp64(torch, ctx, flavor):
+    """BASELINE tolerance: chi at eta = 10 meV within 1e-8 of the oracle (C1, 50 steps)."""
+    from oracle.spectrum import chi_banded, omega_grid_mev, HA_MEV
+    q = slot(ctx, "C1")
+    got = ctx.lanczos_run([q], [1], 50, flavor)
+    chi = ctx.spectrum(got, 0.0, 2000.0, 2.0, 10.0, units=1)[0]
+    ref_c = _oracle_chain("C1", 1, 50, flavor)
+    om = omega_grid_mev(0.0, 2000.0, 2.0) / HA_MEV
+    ref = chi_banded(ref_c, om, 10.0 / HA_MEV, liouvillian("C1").gs.wk[0])
+    err = np.linalg.norm(chi - ref) / np.linalg.norm(ref[1])
+    assert err <= 1e-8, err
+
+
+def test_invalid_inputs_rejected(torch, ctx):
+    import dataclasses
+    from paper_2203_01120_gb300 import TdlzError
+    gs = ground_state("C0")
+    bad_q = dataclasses.replace(gs, q=np.zeros(3))
+    with pytest.raises(TdlzError) as e:
+        ctx.load_ground_state(bad_q)
+    assert e.value.status == 1
+    bad_npw = dataclasses.replace(gs, npw_kq=gs.npw_kq + gs.npwx)
+    with pytest.raises(TdlzError):
+        ctx.load_ground_state(bad_npw)
+    d = gs.dnl.copy()
+    d[0, 1] += 0.1
+    with pytest.raises(TdlzError):
+        ctx.load_ground_state(dataclasses.replace(gs, dnl=d))
+    q = slot(ctx, "C0")
+    x = __import__("torch").zeros(10, dtype=__import__("torch").complex128, device="cuda")
+    with pytest.raises(TdlzError):
+        ctx.apply_liouvillian(q, x, x)  # overlapping x, y
