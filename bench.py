@@ -119,7 +119,7 @@ def measured_peaks():
 def make_workload(cfg, tol):
     from synth import make_ground_state
     t = time.time()
-    gs = make_ground_state(cfg, tol=tol, log=None)
+    gs = make_ground_state(cfg, tol=tol, log=log)
     log(f"[bench] ground state {cfg}: npwx={gs.npwx} nk={gs.nk} nocc={gs.nocc} "
         f"gap={gs.meta['gap_min']:.3e} resid={gs.meta['resid_max']:.2e} "
         f"({time.time() - t:.1f} s)")

@@ -230,8 +230,13 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
                         torch = _torch
                         if device is None:
                             device = "cuda" if torch.cuda.is_available() else "cpu"
+                    import time as _time
+                    _t0 = _time.time()
                     w, v, res = _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield,
-                                           beta, dnl, nb, tol, rng, log)
+                                           beta, dnl, nb, tol, rng, None)
+                    if log is not None:
+                        log(f"  H(k={ik}, {'k+q' if which else 'k'}, side {'XY'[side]}): "
+                            f"npw {npw}, resid {res:.1e}, {_time.time() - _t0:.1f} s on {device}")
                 resid_max = max(resid_max, float(res))
                 gaps.append(float(w[nb] - w[nb - 1]))
                 vec = v[:, :nb].T.reshape(nb, 2, npw)
