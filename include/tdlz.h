@@ -183,6 +183,31 @@ tdlz_status tdlz_lanczos_run(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_l
 tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectrum_params *sp,
                           double *chi, int *nomega);
 
+/* ---- allocation-free spectrum (the paper has no counterpart: it concerns the
+ * callers of this library, not the method).
+ * Same result as tdlz_spectrum, for callers that must not allocate device
+ * memory: an application whose device memory is owned entirely by another
+ * allocator (a framework's caching pool, or a fixed budget handed out up
+ * front), or a latency-bound loop that cannot take the device-wide
+ * synchronisation that cudaMalloc / cudaFree imply.  Coefficients and chi are
+ * caller-owned DEVICE arrays (layouts as in tdlz_coeffs / tdlz_spectrum,
+ * complex double); nomega must equal the grid length (query it with
+ * tdlz_spectrum(ctx, c, sp, NULL, &nomega), which allocates nothing).
+ * Scratch: one file-scope static device array of TDLZ_NOALLOC_SCRATCH_MB MiB,
+ * held by every GPU that loads the library until the process exits; frequencies
+ * are processed in chunks that fit it.  Rejected with TDLZ_ERR_ARG (nothing
+ * launched): 4 * nchain * nsteps complex rows above the scratch, i.e.
+ * nchain * nsteps > TDLZ_NOALLOC_SCRATCH_MB * 2^20 / 64.  The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call on a
+ * device shares the one array and leaves its contents behind (each call writes
+ * every row it reads, so nothing needs clearing); calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race on it.  Enqueued on the
+ * context stream; no allocation of any kind, no synchronisation. */
+#define TDLZ_NOALLOC_SCRATCH_MB 32
+tdlz_status tdlz_spectrum_noalloc(tdlz_ctx *ctx, const tdlz_coeffs *dev_coeffs,
+                                  const tdlz_spectrum_params *sp, double *dev_chi, int nomega);
+
 /* ---- measurement (no counterpart in the paper, whose own numbers are wall
  * times only): per-stage device time from CUDA events recorded on the context
  * stream around each stage, with the stage's algorithmic bytes and flops. */

@@ -79,6 +79,8 @@ EXPORTS = {
                                    C.POINTER(TdlzLanczosResult)]),
     "tdlz_spectrum": (C.c_int, [C.c_void_p, C.POINTER(TdlzCoeffs),
                                 C.POINTER(TdlzSpectrumParams), _dp, _ip]),
+    "tdlz_spectrum_noalloc": (C.c_int, [C.c_void_p, C.POINTER(TdlzCoeffs),
+                                        C.POINTER(TdlzSpectrumParams), C.c_void_p, C.c_int]),
     "tdlz_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "tdlz_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), _dp, _dp]),
     "tdlz_stage_name": (C.c_char_p, [C.c_int]),
@@ -257,6 +259,32 @@ class Context:
         self._check(self.lib.tdlz_spectrum(self.h, C.byref(c), C.byref(sp),
                                            _dptr(chi.view(np.float64)), C.byref(nw)))
         return chi
+
+
+    def spectrum_noalloc(self, dev, start, end, step, eta, units, chi_dev):
+        """tdlz_spectrum_noalloc: every array in ``dev`` and ``chi_dev`` is a CUDA tensor
+        the caller allocated (steps int32, alpha/gamma/z complex128, beta/n0/wk float64);
+        chi_dev is complex128 [nchain][3][nomega].  Enqueued on the context stream."""
+        nc, cap = dev["beta"].shape
+        vp = lambda t: C.cast(C.c_void_p(t.data_ptr()), _dp)  # noqa: E731
+        c = TdlzCoeffs(nc, cap, C.cast(C.c_void_p(dev["steps_done"].data_ptr()), _ip),
+                       vp(dev["alpha"]), vp(dev["beta"]), vp(dev["gamma"]), vp(dev["z"]),
+                       vp(dev["n0"]), vp(dev["wk"]))
+        sp = TdlzSpectrumParams(float(start), float(end), float(step), float(eta), int(units))
+        self._check(self.lib.tdlz_spectrum_noalloc(self.h, C.byref(c), C.byref(sp),
+                                                   C.c_void_p(chi_dev.data_ptr()),
+                                                   int(chi_dev.shape[-1])))
+
+    def spectrum_nomega(self, start, end, step, units=1):
+        """Frequency-grid length (tdlz_spectrum with chi = NULL; allocates nothing)."""
+        one = np.zeros(1)
+        onei = np.zeros(1, np.int32)
+        c = TdlzCoeffs(1, 1, _iptr(onei), _dptr(one), _dptr(one), _dptr(one), _dptr(one),
+                       _dptr(one), _dptr(one))
+        sp = TdlzSpectrumParams(float(start), float(end), float(step), 1.0, int(units))
+        nw = C.c_int()
+        self._check(self.lib.tdlz_spectrum(self.h, C.byref(c), C.byref(sp), None, C.byref(nw)))
+        return nw.value
 
 
 class Chain:

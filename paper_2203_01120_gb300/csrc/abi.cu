@@ -123,6 +123,11 @@ tdlz_status tdlz_profile_read(tdlz_ctx *ctx, double *ms, int64_t *launches, doub
   });
 }
 
+tdlz_status tdlz_spectrum_noalloc(tdlz_ctx *ctx, const tdlz_coeffs *dev_coeffs,
+                                  const tdlz_spectrum_params *sp, double *dev_chi, int nomega) {
+  return guarded(ctx, [&] { spectrum_noalloc(ctx->c, dev_coeffs, sp, dev_chi, nomega); });
+}
+
 const char *tdlz_stage_name(int stage) { return stage_name(stage); }
 
 int64_t tdlz_launch_count(void) { return g_launches.load(); }

@@ -137,6 +137,10 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool ad
 template <class T> void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v);
 void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs);
 
+// --- allocation-free spectrum (spectrum_noalloc.cu) ---
+void spectrum_noalloc(Context &ctx, const tdlz_coeffs *c, const tdlz_spectrum_params *sp,
+                      double *chi, int nomega);
+
 // --- vector helpers (lanczos.cu) ---
 template <class T>
 void jflip_copy(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y);
