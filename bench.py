@@ -4,8 +4,9 @@
 Workload (default): the C2 CrI3-shaped synthetic crystal -- hexagonal a = 13 bohr,
 c = 30 bohr (vacuum slab), FFT 36x36x96, ~5000 plane waves per spinor component,
 4x4 k grid (16 k), 40 occupied spinor bands, 8 atoms x 8 KB projectors with
-spin-orbit, q = (1/8, 0, 0) 2pi/a.  A step is one pseudo-Hermitian Lanczos
-iteration of one chain (one Liouvillian application + the FP64 scalar update).
+spin-orbit, q = (1/8, 0, 0) 2pi/a.  A step is one Lanczos iteration of one chain
+and its FP64 scalar update: two Liouvillian applications (L q and L^H p) for the
+non-Hermitian flavour used by default, one for the pseudo-Hermitian flavours.
 
 Reported (one JSON line on rank 0):
   value          mixed-precision steps/s (FP32 vectors and arithmetic, FP64 scalars)
@@ -35,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Lanczos steps/s and %HBM roofline, mixed vs FP64 at rel chi(w) err <=1e-4"
 WORKLOAD = ("C2: hexagonal a=13 c=30 bohr, FFT 36x36x96, ~5000 PW/component, 4x4 k, "
-            "Nocc=40, 8 atoms x 8 KB projectors with SOC, q=(1/8,0,0) 2pi/a, PH Lanczos")
+            "Nocc=40, 8 atoms x 8 KB projectors with SOC, q=(1/8,0,0) 2pi/a")
 
 
 def parse():
@@ -45,10 +46,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tdlz", choices=["tdlz", "reference"])
     ap.add_argument("--config", default="C2")
-    ap.add_argument("--flavor", default="phm", choices=["ph", "phm", "nh"])
+    # NH by default: on the synthetic C2 model D + K is indefinite (the positive-definite
+    # metric does not exist) and the J-metric start vector has a J-norm ~1e-3 of its norm
+    ap.add_argument("--flavor", default="nh", choices=["ph", "phm", "nh"])
     ap.add_argument("--chi-steps", type=int, default=60)
+    ap.add_argument("--chains", type=int, default=3, choices=[1, 2, 3],
+                    help="chi columns per GPU (x, y, z), advanced together")
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bundle", default=None, help="cache file for the generated ground state")
+    ap.add_argument("--profile-apply", type=int, default=0,
+                    help="run N Liouvillian applications on a shape-only bundle (for profilers)")
+    ap.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
+    ap.add_argument("--kpoints", type=int, default=0,
+                    help="profile-apply: keep only the first N k points (smaller device footprint)")
     return ap.parse_args()
 
 
@@ -107,6 +118,24 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """Largest value over the ranks of the default process group (the value itself
+    without one).  The bench times every rank and reports the slowest."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, chains: int, steps: int, max_wall: float) -> float:
+    """Chain-steps per second of the whole job: every rank advances its own chains
+    (replicas, weak scaling), the job lasts as long as its slowest rank."""
+    return world * chains * steps / max_wall
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -116,10 +145,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def make_workload(cfg, tol):
-    from synth import make_ground_state
+def make_workload(cfg, tol, bundle=None):
+    from synth import GroundState, make_ground_state
     t = time.time()
+    if bundle and os.path.exists(bundle):
+        gs = GroundState.load(bundle)
+        gs.meta = {"gap_min": float("nan"), "resid_max": float("nan")}
+        log(f"[bench] ground state {cfg} loaded from {bundle}")
+        return gs
     gs = make_ground_state(cfg, tol=tol, log=log)
+    if bundle:
+        gs.save(bundle)
     log(f"[bench] ground state {cfg}: npwx={gs.npwx} nk={gs.nk} nocc={gs.nocc} "
         f"gap={gs.meta['gap_min']:.3e} resid={gs.meta['resid_max']:.2e} "
         f"({time.time() - t:.1f} s)")
@@ -177,7 +213,7 @@ def run_reference(args):
     if rank != 0:
         return
     import numpy as np  # noqa: F401
-    gs = make_workload(args.config, args.tol)
+    gs = make_workload(args.config, args.tol, args.bundle)
     cores, model = cpu_info()
     times = []
     for i in range(args.warmup + args.steps):
@@ -202,18 +238,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def chain_steps_per_s(ctx, q, mu, flavor, precision, warmup, steps, profile=False):
-    import torch  # noqa: F401
-    ch = ctx.chain_create([q], [mu], warmup + steps + 1, flavor, precision)
+def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, profile=False):
+    """Chain-steps per second summed over the chains mus (one group on one q-slot).
+    The library runs on its own stream; the timed region is bracketed by
+    synchronisations of that stream (tdlz_synchronize) on both sides."""
+    ch = ctx.chain_create([q] * len(mus), mus, warmup + steps + 1, flavor, precision)
     try:
         ch.advance(warmup)
         ctx.synchronize()
         if profile:
             ctx.profile(True)
         l0 = ctx.launch_count()
-        start = __import__("torch").cuda.Event(enable_timing=True)
-        end = __import__("torch").cuda.Event(enable_timing=True)
-        # the library runs on its own stream; bracket with device syncs + events on it
         ctx.synchronize()
         t0 = time.perf_counter()
         ch.advance(steps)
@@ -224,8 +259,7 @@ def chain_steps_per_s(ctx, q, mu, flavor, precision, warmup, steps, profile=Fals
         if profile:
             ctx.profile(False)
         res = ch.read()
-        del start, end
-        return steps / wall, wall, launches, prof, res
+        return len(mus) * steps / wall, wall, launches, prof, res
     finally:
         ch.close()
 
@@ -240,13 +274,14 @@ def run_tdlz(args):
     torch.cuda.set_device(local)
     from paper_2203_01120_gb300 import TDLZ_FP64, TDLZ_MIXED, Context, build_ext
     build_ext.build()
-    gs = make_workload(args.config, args.tol)
-    mu = rank % 3  # replicas: each rank runs its own column of chi
+    gs = make_workload(args.config, args.tol, args.bundle)
+    # replicas: every rank runs the chi columns mus (the paper's ipol = 4: x, y, z)
+    mus = list(range(args.chains))
     ctx = Context(local)
     # ------------------------------------------------------------ e2e (host in/out)
     t0 = time.perf_counter()
     q = ctx.load_ground_state(gs)
-    ch = ctx.chain_create([q], [mu], args.steps, args.flavor, TDLZ_MIXED)
+    ch = ctx.chain_create([q] * len(mus), mus, args.steps, args.flavor, TDLZ_MIXED)
     ch.advance(args.steps)
     res_e2e = ch.read()
     e2e_wall = time.perf_counter() - t0
@@ -254,32 +289,30 @@ def run_tdlz(args):
     bundle_bytes = sum(int(np.asarray(getattr(gs, k)).nbytes) for k in (
         "kpts", "wk", "npw_k", "npw_kq", "miller_k", "miller_kq", "evals", "coeff_k", "coeff_kq",
         "vloc", "bfield", "n0", "m0", "beta_kq", "dnl"))
-    coef_bytes = args.steps * (16 * 2 + 8 + 16 * 3)
+    coef_bytes = len(mus) * args.steps * (16 * 2 + 8 + 16 * 3)
     # ------------------------------------------------------------ device-resident timing
     if world > 1:
         torch.distributed.barrier()
     clk = ClockSampler(local)
     clk.start()
     sps_mixed, wall_mixed, launches, _, _ = chain_steps_per_s(
-        ctx, q, mu, args.flavor, TDLZ_MIXED, args.warmup, args.steps)
+        ctx, q, mus, args.flavor, TDLZ_MIXED, args.warmup, args.steps)
     clocks = clk.finish()
-    if world > 1:
-        t = torch.tensor([wall_mixed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        wall_mixed = float(t.item())
+    wall_mixed = max_over_ranks(wall_mixed, "cuda")
     # profiled pass (per-stage CUDA events on the library stream) for the roofline
-    _, _, _, prof, _ = chain_steps_per_s(ctx, q, mu, args.flavor, TDLZ_MIXED, 1, args.steps,
+    _, _, _, prof, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_MIXED, 1, args.steps,
                                          profile=True)
     fp64_steps = max(3, args.steps // 4)
-    sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(ctx, q, mu, args.flavor, TDLZ_FP64, 1,
+    sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_FP64, 1,
                                                           fp64_steps, profile=True)
     # ------------------------------------------------------------ chi error mixed vs FP64
     m = args.chi_steps
-    r64 = ctx.lanczos_run([q], [mu], m, args.flavor, TDLZ_FP64)
-    r32 = ctx.lanczos_run([q], [mu], m, args.flavor, TDLZ_MIXED)
-    c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1)[0]
-    c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)[0]
-    chi_err = float(np.linalg.norm(c32 - c64) / np.linalg.norm(c64[mu]))
+    r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)
+    r32 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
+    c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1)
+    c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)
+    chi_err = max(float(np.linalg.norm(c32[i] - c64[i]) / np.linalg.norm(c64[i][mu]))
+                  for i, mu in enumerate(mus))
     ctx.close()
     if rank != 0:
         return
@@ -303,12 +336,16 @@ def run_tdlz(args):
                          f"{gs.nk}, {el:.1f} s, scaled x{gs.nk} (cost linear in k)",
                "cpu": model}
     line = {
-        "metric": METRIC, "value": world * args.steps / wall_mixed if world > 1 else sps_mixed,
+        "metric": METRIC,
+        "value": whole_job_rate(world, len(mus), args.steps, wall_mixed),
+        "l_applications_per_s": whole_job_rate(world, len(mus), args.steps, wall_mixed)
+        * (2 if args.flavor == "nh" else 1),
         "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * wall_mixed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "flavor": args.flavor, "precision": "mixed",
-                   "chains_per_gpu": 1, "parallelism": f"replicas{world}",
+                   "chains_per_gpu": len(mus), "parallelism": f"replicas{world}",
+                   "ms_per_step_is": "one step of every chain of the GPU (advanced together)",
                    "l2": "inputs larger than L2 (per-step working set > 5 GB)"},
         "fp64": {"value": sps_fp64, "unit": "steps/s", "steps": fp64_steps,
                  "ms_per_step": 1000 * wall_fp64 / fp64_steps},
@@ -323,19 +360,54 @@ def run_tdlz(args):
         "stages_fp64_ms_per_step": {k: round(v["ms"] / fp64_steps, 4) for k, v in prof64.items()
                                     if v["launches"]},
         "clocks": clocks, "gpu_launches": launches,
-        "e2e": {"value": args.steps / e2e_wall, "unit": "steps/s",
+        "e2e": {"value": len(mus) * args.steps / e2e_wall, "unit": "steps/s",
                 "h2d_bytes_per_step": bundle_bytes / args.steps,
                 "d2h_bytes_per_step": coef_bytes / args.steps,
                 "what": "load_ground_state(host bundle) + chain of K mixed steps + coefficients "
                         "to host, through the C ABI"},
         "cpu_baseline": cpu,
-        "status": int(res_e2e["status"][0]),
+        "status": [int(v) for v in res_e2e["status"]],
     }
     print(json.dumps(line), flush=True)
 
 
+def run_profile_apply(args):
+    """Small, self-contained case for profilers: a shape-only bundle of the config
+    (random orthonormal occupied states, no diagonalisation) and a few Liouvillian
+    applications per precision.  Used by the ncu summaries under profiles/."""
+    import numpy as np
+    import torch
+    from paper_2203_01120_gb300 import TDLZ_FP64, TDLZ_MIXED, Context, build_ext
+    from synth import make_ground_state, random_br_vector
+    build_ext.build()
+    gs = make_ground_state(args.config, solver="random")
+    if args.kpoints:
+        gs = sample_bundle(gs, args.kpoints)
+    ctx = Context(0)
+    q = ctx.load_ground_state(gs)
+    x = random_br_vector(gs, seed=7)
+    precs = {"mixed": [TDLZ_MIXED], "fp64": [TDLZ_FP64], "both": [TDLZ_MIXED, TDLZ_FP64]}
+    for prec in precs[args.precision]:
+        dt = torch.complex64 if prec == TDLZ_MIXED else torch.complex128
+        xt = torch.as_tensor(x, dtype=dt, device="cuda")
+        yt = torch.zeros_like(xt)
+        ctx.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.profile_apply):
+            ctx.apply_liouvillian(q, xt, yt, False, prec)
+        ctx.synchronize()
+        dt_ms = 1000 * (time.perf_counter() - t) / args.profile_apply
+        log(f"[profile-apply] {args.config} {'mixed' if prec else 'fp64'}: {dt_ms:.3f} ms per L "
+            f"(|y| = {float(torch.linalg.vector_norm(yt)):.4e})")
+    ctx.close()
+    del np
+
+
 def main():
     args = parse()
+    if args.profile_apply:
+        run_profile_apply(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

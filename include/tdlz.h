@@ -136,10 +136,19 @@ typedef struct {
 } tdlz_coeffs;
 
 /* Frequencies start..end step `step` (inclusive), broadening eta; units 0 = Ha,
- * 1 = meV (1 Ha = 27211.386245988 meV). */
+ * 1 = meV (1 Ha = 27211.386245988 meV).
+ * itermax0, itermax, extrapolation: the paper's post-processing options (Sec. 3.3).
+ * itermax0 = number of computed coefficients used (0 = all computed steps);
+ * extrapolation 0 = none, 1 = constant, 2 = bi-constant ("osc"): coefficients
+ * itermax0 .. itermax-1 are the means of the computed ones over the window
+ * [itermax0/2, itermax0) (per index parity for the bi-constant form) and z = 0
+ * there; the tail is folded into the last computed row by its continued
+ * fraction, so itermax may exceed the stored steps at no memory cost.
+ * tdlz_spectrum_noalloc supports itermax0 = 0 and extrapolation = 0 only. */
 typedef struct {
   double start, end, step, eta;
   int units;
+  int itermax0, itermax, extrapolation;
 } tdlz_spectrum_params;
 
 /* Create a context on CUDA device `device`.  cuda_stream (a cudaStream_t) may be
@@ -172,6 +181,18 @@ tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_
 tdlz_status tdlz_chain_advance(tdlz_chain *ch, int nsteps); /* enqueue nsteps steps */
 tdlz_status tdlz_chain_read(tdlz_chain *ch, tdlz_lanczos_result *res); /* synchronises */
 void tdlz_chain_destroy(tdlz_chain *ch);
+
+/* Restart (the paper's restart / restart_step, Table of turbo_magnon.x inputs):
+ * the chains' full state -- Lanczos vectors, device scalars and the
+ * coefficients so far -- as one host image.  tdlz_chain_save synchronises and
+ * copies into a caller-owned HOST buffer of tdlz_chain_state_size bytes.
+ * tdlz_chain_restore loads an image into a chain set created with the same
+ * q-slots, mu, flavour and precision and a capacity (nsteps) >= the saved one;
+ * advancing it then continues the recursion exactly where it stopped (FP64 and
+ * mixed resumes are bitwise identical to an uninterrupted run). */
+tdlz_status tdlz_chain_state_size(tdlz_chain *ch, int64_t *bytes);
+tdlz_status tdlz_chain_save(tdlz_chain *ch, void *host_image, int64_t bytes);
+tdlz_status tdlz_chain_restore(tdlz_chain *ch, const void *host_image, int64_t bytes);
 
 /* create + advance(nsteps) + read + destroy. */
 tdlz_status tdlz_lanczos_run(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_lanczos_result *res);

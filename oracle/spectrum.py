@@ -85,3 +85,57 @@ def omega_grid_mev(start, end, step):
 def chi(coef, omegas, eta, w, m=None):
     """Primary oracle spectrum: the pivoted banded solve (robust for every flavour)."""
     return chi_banded(coef, omegas, eta, w, m)
+
+
+# --------------------------------------------------------------- extrapolation
+# Sec. 3.3 of the paper: the first itermax0 coefficients are the computed ones; up
+# to itermax the chain is continued with extrapolated coefficients, either one
+# constant ('constant') or two alternating constants ('osc', bi-constant), and the
+# z coefficients are zero beyond itermax0.  Reading (the averaging window is not
+# given): the constants are the means over the last half of the computed
+# coefficients, [itermax0 // 2, itermax0), taken over all indices for 'constant'
+# and separately over even and odd indices for 'osc'.
+
+def extrapolation_constants(coef, itermax0, kind):
+    """Returns {parity: (alpha, beta, gamma)} with parity 0/1 (same for 'constant')."""
+    lo = itermax0 // 2
+    idx = np.arange(lo, itermax0)
+    out = {}
+    for parity in (0, 1):
+        sel = idx if kind == "constant" else idx[idx % 2 == parity]
+        out[parity] = (np.mean(coef.alpha[sel]), np.mean(coef.beta[sel]),
+                       np.mean(coef.gamma[sel]))
+    return out
+
+
+def extend_coefficients(coef, itermax0, itermax, kind):
+    """Explicitly extended coefficient arrays of length itermax."""
+    import dataclasses
+    if kind == "no" or itermax <= itermax0:
+        m = min(itermax0, coef.steps)
+        return dataclasses.replace(coef, alpha=coef.alpha[:m], beta=coef.beta[:m],
+                                   gamma=coef.gamma[:m], z=coef.z[:, :m], steps=m)
+    if itermax0 > coef.steps:
+        raise ValueError("itermax0 exceeds the computed coefficients")
+    c = extrapolation_constants(coef, itermax0, kind)
+    al = np.zeros(itermax, dtype=np.complex128)
+    be = np.zeros(itermax)
+    ga = np.zeros(itermax, dtype=np.complex128)
+    z = np.zeros((coef.z.shape[0], itermax), dtype=np.complex128)
+    al[:itermax0] = coef.alpha[:itermax0]
+    # beta[j] (= beta_{j+2}) links steps j and j+1; the chain computed it for
+    # j < itermax0 (its last step yields the link to the first extrapolated step)
+    be[:itermax0] = coef.beta[:itermax0]
+    ga[:itermax0] = coef.gamma[:itermax0]
+    z[:, :itermax0] = coef.z[:, :itermax0]
+    for j in range(itermax0, itermax):
+        al[j] = c[j % 2][0]
+        be[j] = c[j % 2][1].real
+        ga[j] = c[j % 2][2]
+    return dataclasses.replace(coef, alpha=al, beta=be, gamma=ga, z=z, steps=itermax)
+
+
+def chi_extrapolated(coef, omegas, eta, w, itermax0, itermax, kind):
+    """chi from the explicitly extended tridiagonal system (pivoted banded solve)."""
+    ext = extend_coefficients(coef, itermax0, itermax, kind)
+    return chi_banded(ext, omegas, eta, w)

@@ -58,7 +58,11 @@ class TdlzCoeffs(C.Structure):
 
 class TdlzSpectrumParams(C.Structure):
     _fields_ = [("start", C.c_double), ("end", C.c_double), ("step", C.c_double),
-                ("eta", C.c_double), ("units", C.c_int)]
+                ("eta", C.c_double), ("units", C.c_int), ("itermax0", C.c_int),
+                ("itermax", C.c_int), ("extrapolation", C.c_int)]
+
+
+EXTRAPOLATION = {"no": 0, "constant": 1, "osc": 2}
 
 
 EXPORTS = {
@@ -75,6 +79,9 @@ EXPORTS = {
     "tdlz_chain_advance": (C.c_int, [C.c_void_p, C.c_int]),
     "tdlz_chain_read": (C.c_int, [C.c_void_p, C.POINTER(TdlzLanczosResult)]),
     "tdlz_chain_destroy": (None, [C.c_void_p]),
+    "tdlz_chain_state_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "tdlz_chain_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "tdlz_chain_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "tdlz_lanczos_run": (C.c_int, [C.c_void_p, C.POINTER(TdlzLanczosParams),
                                    C.POINTER(TdlzLanczosResult)]),
     "tdlz_spectrum": (C.c_int, [C.c_void_p, C.POINTER(TdlzCoeffs),
@@ -240,7 +247,8 @@ class Context:
         finally:
             ch.close()
 
-    def spectrum(self, coeffs, start, end, step, eta, units=1):
+    def spectrum(self, coeffs, start, end, step, eta, units=1, itermax0=0, itermax=0,
+                 extrapolation="no"):
         """chi[nchain][3][nomega] from a coefficient dict as returned by Chain.read()."""
         nc, cap = coeffs["beta"].shape
         steps = np.ascontiguousarray(coeffs["steps_done"], dtype=np.int32)
@@ -252,7 +260,8 @@ class Context:
         wk = np.ascontiguousarray(coeffs["wk"], dtype=np.float64)
         c = TdlzCoeffs(nc, cap, _iptr(steps), _dptr(al.view(np.float64)), _dptr(be),
                        _dptr(ga.view(np.float64)), _dptr(z.view(np.float64)), _dptr(n0), _dptr(wk))
-        sp = TdlzSpectrumParams(float(start), float(end), float(step), float(eta), int(units))
+        sp = TdlzSpectrumParams(float(start), float(end), float(step), float(eta), int(units),
+                                int(itermax0), int(itermax), EXTRAPOLATION[extrapolation])
         nw = C.c_int()
         self._check(self.lib.tdlz_spectrum(self.h, C.byref(c), C.byref(sp), None, C.byref(nw)))
         chi = np.zeros((nc, 3, nw.value), dtype=np.complex128)
@@ -319,6 +328,18 @@ class Chain:
                               _iptr(out["status"]))
         self.ctx._check(self.ctx.lib.tdlz_chain_read(self.h, C.byref(r)))
         return out
+
+    def save(self) -> bytes:
+        """Restart image of the chains (host bytes)."""
+        n = C.c_int64()
+        self.ctx._check(self.ctx.lib.tdlz_chain_state_size(self.h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self.ctx._check(self.ctx.lib.tdlz_chain_save(self.h, buf, n.value))
+        return buf.raw
+
+    def restore(self, image: bytes):
+        buf = C.create_string_buffer(image, len(image))
+        self.ctx._check(self.ctx.lib.tdlz_chain_restore(self.h, buf, len(image)))
 
     def close(self):
         if self.h:

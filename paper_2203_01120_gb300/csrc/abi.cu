@@ -174,9 +174,9 @@ tdlz_status tdlz_apply_liouvillian(tdlz_ctx *ctx, int qslot, const void *x, void
                      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged),
                  TDLZ_ERR_ARG, "y is not device memory");
     if (precision == TDLZ_FP64)
-      apply_liouvillian<double>(ctx->c, s, (const double2 *)x, (double2 *)y, adjoint != 0);
+      apply_liouvillian<double>(ctx->c, s, (const double2 *)x, (double2 *)y, 1, adjoint ? 1u : 0u);
     else
-      apply_liouvillian<float>(ctx->c, s, (const float2 *)x, (float2 *)y, adjoint != 0);
+      apply_liouvillian<float>(ctx->c, s, (const float2 *)x, (float2 *)y, 1, adjoint ? 1u : 0u);
   });
 }
 
@@ -192,6 +192,10 @@ tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_
     for (int c = 0; c < p->nchain; ++c) {
       slot_of(ctx, p->qslot[c]);
       TDLZ_REQUIRE(p->mu[c] >= 0 && p->mu[c] <= 2, TDLZ_ERR_ARG, "mu must be 0, 1 or 2");
+      int same = 0;
+      for (int d = 0; d < p->nchain; ++d) same += p->qslot[d] == p->qslot[c];
+      TDLZ_REQUIRE(same <= (p->flavor == TDLZ_NONHERMITIAN ? 16 : 32), TDLZ_ERR_ARG,
+                   "at most 16 NH (32 PH) chains per q-slot in one chain set");
     }
     ch = new tdlz_chain();
     ch->owner = ctx;
@@ -230,6 +234,30 @@ tdlz_status tdlz_chain_read(tdlz_chain *ch, tdlz_lanczos_result *res) {
   });
 }
 
+tdlz_status tdlz_chain_state_size(tdlz_chain *ch, int64_t *bytes) {
+  if (!ch) return TDLZ_ERR_ARG;
+  return guarded(ch->owner, [&] {
+    TDLZ_REQUIRE(bytes != nullptr, TDLZ_ERR_ARG, "NULL output");
+    *bytes = (int64_t)ch->set.state_bytes();
+  });
+}
+
+tdlz_status tdlz_chain_save(tdlz_chain *ch, void *host_image, int64_t bytes) {
+  if (!ch) return TDLZ_ERR_ARG;
+  return guarded(ch->owner, [&] {
+    TDLZ_REQUIRE(host_image != nullptr && bytes > 0, TDLZ_ERR_ARG, "NULL or empty image");
+    ch->set.save(host_image, (size_t)bytes);
+  });
+}
+
+tdlz_status tdlz_chain_restore(tdlz_chain *ch, const void *host_image, int64_t bytes) {
+  if (!ch) return TDLZ_ERR_ARG;
+  return guarded(ch->owner, [&] {
+    TDLZ_REQUIRE(host_image != nullptr && bytes > 0, TDLZ_ERR_ARG, "NULL or empty image");
+    ch->set.restore(host_image, (size_t)bytes);
+  });
+}
+
 void tdlz_chain_destroy(tdlz_chain *ch) {
   if (!ch) return;
   cudaSetDevice(ch->owner->c.device);
@@ -257,6 +285,10 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
     TDLZ_REQUIRE(sp->step > 0 && sp->end >= sp->start && std::isfinite(sp->eta) && sp->eta > 0,
                  TDLZ_ERR_ARG, "need step > 0, end >= start and eta > 0");
     TDLZ_REQUIRE(sp->units == 0 || sp->units == 1, TDLZ_ERR_ARG, "units must be 0 (Ha) or 1 (meV)");
+    TDLZ_REQUIRE(sp->extrapolation >= 0 && sp->extrapolation <= 2 && sp->itermax0 >= 0,
+                 TDLZ_ERR_ARG, "extrapolation must be 0, 1 or 2 and itermax0 >= 0");
+    TDLZ_REQUIRE(sp->extrapolation == 0 || (sp->itermax0 >= 2 && sp->itermax >= sp->itermax0),
+                 TDLZ_ERR_ARG, "extrapolation needs itermax0 >= 2 and itermax >= itermax0");
     long long nw = (long long)std::floor((sp->end - sp->start) / sp->step + 0.5) + 1;
     TDLZ_REQUIRE(nw >= 1 && nw <= (1 << 24), TDLZ_ERR_ARG, "frequency grid too long");
     *nomega = (int)nw;
@@ -296,6 +328,12 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
     a.step = sp->step * conv;
     a.eta = sp->eta * conv;
     a.scratch = d_scr.as<double2>();
+    a.itermax0 = sp->itermax0;
+    a.itermax = sp->itermax;
+    a.extrap = sp->extrapolation;
+    for (int i = 0; i < nc; ++i)
+      TDLZ_REQUIRE(sp->itermax0 <= c->steps[i] || sp->itermax0 == 0 || sp->extrapolation == 0,
+                   TDLZ_ERR_ARG, "itermax0 exceeds the computed steps of a chain");
     a.chi = d_chi.as<double2>();
     launch_spectrum(st, a);
     TDLZ_CUDA_TRY(cudaMemcpyAsync(chi, d_chi.p, sizeof(double2) * nc * 3 * nw,

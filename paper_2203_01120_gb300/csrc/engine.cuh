@@ -74,7 +74,8 @@ template <class T> struct SlotData {
 
 template <class T> struct Workspace {
   DevBuf xr;    // [2][nk][nb][2][Nr] real-space response orbitals
-  DevBuf rho;   // [4][Nr]
+  DevBuf rho;   // [nvec][4][Nr]
+  DevBuf rhopart;  // [groups][nvec][4][Nr] partial densities
   DevBuf vpot;  // [4][Nr]
   DevBuf hgrid; // [Nr] Hartree scratch
   DevBuf h;     // [BR] sphere intermediate
@@ -83,6 +84,9 @@ template <class T> struct Workspace {
   DevBuf dmix;  // [2nk][2nb][nproj]
   DevBuf ovl;   // [2nk][nb][nb]      <U_kq|h>
   DevBuf part;  // split-K partial sums
+  DevBuf i1;    // [rows][nstick_max][n3] stick scratch
+  DevBuf i2;    // [rows][nplane_max][n2][n3] plane scratch
+  int nvec_cap = 0;  // stacked vectors the buffers above are sized for
   bool ready = false;
 };
 
@@ -98,6 +102,14 @@ struct QSlot {
   DevBuf map_kq_k;       // [nk][npwx] int32: index of the same G in the k sphere or -1
   DevBuf npwkq_d;        // [nk] int32
   DevBuf coeff_k;        // [2][nk][nb][2][npwx] occupied k spinors (FP64; start vectors)
+  // stick / plane tables of the k+q spheres (pipeline.cu)
+  int nstick_max = 0, nplane_max = 0;
+  DevBuf st_n;    // [nk] sticks per k
+  DevBuf st_map;  // [nk][nstick_max][n3] sphere index of (stick, j3) or -1
+  DevBuf pl_n;    // [nk] planes per k
+  DevBuf pl_j1;   // [nk][nplane_max] grid index j1 of each plane
+  DevBuf pl_of;   // [nk][n1] plane index of j1 or -1
+  DevBuf st_id;   // [nk][nplane_max][n2] stick index of (plane, j2) or -1
   FFTPlan plan;
   SlotData<double> d64;
   SlotData<float> d32;
@@ -132,8 +144,11 @@ template <class T> inline Workspace<T> &slot_ws(QSlot &s) {
 
 // --- Liouvillian (liouvillian.cu) ---
 template <class T> void ensure_precision(Context &ctx, QSlot &s);
+// y_v = L x_v (or L^H x_v = J L J x_v where bit v of adj_mask is set) for nvec
+// vectors stacked contiguously in x and y (one BR vector each), in one pass.
 template <class T>
-void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool adjoint);
+void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nvec,
+                       unsigned adj_mask);
 template <class T> void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v);
 void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs);
 

@@ -21,6 +21,7 @@
 //       r = Lq - alpha q - beta q'; w = L r; c = r^H J w; beta' = sqrt c;
 //       q = r/beta', Lq = w/beta' (the product of the step is the one on r).
 #include <cmath>
+#include <cstring>
 
 #include "lanczos.cuh"
 
@@ -42,11 +43,6 @@ struct Pairs {
   int n;
 };
 
-__device__ __forceinline__ double2 load_d(const double2 *p, long long i) { return p[i]; }
-__device__ __forceinline__ double2 load_d(const float2 *p, long long i) {
-  float2 v = p[i];
-  return make_double2(v.x, v.y);
-}
 
 // Block-level deterministic sum of nv complex values per thread into out[blockIdx][nv].
 template <int NV>
@@ -68,22 +64,44 @@ __device__ void block_sum_store(double2 (&v)[NV], double2 *out) {
 }
 
 // partial[blk][i] = sum_{e in blk range} conj(a_i[e]) b_i[e] (J-weighted if requested)
+// Products are formed in the vectors' precision T and summed in T over runs of
+// kRun elements per thread before each run is added to an FP64 accumulator (on
+// this part FP64 arithmetic is ~1/64 of the FP32 rate, so the mixed path keeps
+// the per-element work in FP32 and only the reduction in FP64).
+constexpr int kRun = 16;
 template <class T>
 __global__ void __launch_bounds__(kRedThreads)
     dots_kernel(Pairs pr, long long n, long long half, double2 *partial) {
   double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   long long chunk = (n + gridDim.x - 1) / gridDim.x;
   long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-  for (long long e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
-    double w = e >= half ? -1.0 : 1.0;
+  const int np = pr.n;
+  const cx<T> *A[4], *B[4];
+  T sgn[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    A[i] = reinterpret_cast<const cx<T> *>(pr.p[i].a);
+    B[i] = reinterpret_cast<const cx<T> *>(pr.p[i].b);
+    sgn[i] = pr.p[i].jsign ? T(-1) : T(1);
+  }
+  long long e = b0 + threadIdx.x;
+  while (e < b1) {
+    T rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
+    for (int it = 0; it < kRun && e < b1; ++it, e += blockDim.x) {
+      bool neg = e >= half;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i >= np) break;
+        cx<T> a = A[i][e], b = B[i][e];
+        T s = neg ? sgn[i] : T(1);
+        rx[i] += s * (a.x * b.x + a.y * b.y);
+        ry[i] += s * (a.x * b.y - a.y * b.x);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (i >= pr.n) break;
-      double2 a = load_d(reinterpret_cast<const cx<T> *>(pr.p[i].a), e);
-      double2 b = load_d(reinterpret_cast<const cx<T> *>(pr.p[i].b), e);
-      double s = pr.p[i].jsign ? w : 1.0;
-      acc[i].x += s * (a.x * b.x + a.y * b.y);
-      acc[i].y += s * (a.x * b.y - a.y * b.x);
+      acc[i].x += (double)rx[i];
+      acc[i].y += (double)ry[i];
     }
   }
   block_sum_store<4>(acc, partial);
@@ -270,39 +288,43 @@ __global__ void __launch_bounds__(kRedThreads)
     update_kernel(const cx<T> *a, const cx<T> *q, cx<T> *qp, const cx<T> *b, const cx<T> *p,
                   cx<T> *pp, const ChainScalars *cs, int flavor, long long n, long long half,
                   double2 *partial) {
-  double2 alpha = cs->alpha;
-  double2 g = (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) ? make_double2(cs->beta_prev, 0.0)
-                                                     : cs->gamma_prev;
-  double bp = cs->beta_prev;
+  // coefficients in the vectors' precision (FP64 path: exact; mixed: rounded to FP32,
+  // an error of the order of the FP32 storage of r itself)
+  const double2 a64 = cs->alpha;
+  const double2 g64 = (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) ? make_double2(cs->beta_prev, 0.0)
+                                                            : cs->gamma_prev;
+  const T ax = (T)a64.x, ay = (T)a64.y, gx = (T)g64.x, gy = (T)g64.y, bp = (T)cs->beta_prev;
   double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   long long chunk = (n + gridDim.x - 1) / gridDim.x;
   long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-  for (long long e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
-    double2 av = load_d(a, e), qv = load_d(q, e), qpv = load_d(qp, e);
-    double2 r;
-    r.x = av.x - (alpha.x * qv.x - alpha.y * qv.y) - (g.x * qpv.x - g.y * qpv.y);
-    r.y = av.y - (alpha.x * qv.y + alpha.y * qv.x) - (g.x * qpv.y + g.y * qpv.x);
-    cx<T> rs = mk<T>((T)r.x, (T)r.y);
-    qp[e] = rs;
-    double2 rr = load_d(&rs, 0);  // the stored (rounded) residual
-    double w = e >= half ? -1.0 : 1.0;
-    if (flavor == TDLZ_NONHERMITIAN) {
-      double2 bv = load_d(b, e), pv = load_d(p, e), ppv = load_d(pp, e);
-      double2 t;
-      // t = b - conj(alpha) p - beta p'  (beta real)
-      t.x = bv.x - (alpha.x * pv.x + alpha.y * pv.y) - bp * ppv.x;
-      t.y = bv.y - (alpha.x * pv.y - alpha.y * pv.x) - bp * ppv.y;
-      cx<T> ts = mk<T>((T)t.x, (T)t.y);
-      pp[e] = ts;
-      double2 tt = load_d(&ts, 0);
-      acc[0].x += tt.x * rr.x + tt.y * rr.y;
-      acc[0].y += tt.x * rr.y - tt.y * rr.x;
-      acc[1].x += rr.x * rr.x + rr.y * rr.y;
-      acc[2].x += tt.x * tt.x + tt.y * tt.y;
-    } else {
-      acc[0].x += w * (rr.x * rr.x + rr.y * rr.y);
-      acc[1].x += rr.x * rr.x + rr.y * rr.y;
+  long long e = b0 + threadIdx.x;
+  while (e < b1) {
+    T s0x = 0, s0y = 0, s1 = 0, s2 = 0;
+    for (int it = 0; it < kRun && e < b1; ++it, e += blockDim.x) {
+      cx<T> av = a[e], qv = q[e], qpv = qp[e];
+      cx<T> r = mk<T>(av.x - (ax * qv.x - ay * qv.y) - (gx * qpv.x - gy * qpv.y),
+                      av.y - (ax * qv.y + ay * qv.x) - (gx * qpv.y + gy * qpv.x));
+      qp[e] = r;
+      T rn = r.x * r.x + r.y * r.y;
+      if (flavor == TDLZ_NONHERMITIAN) {
+        cx<T> bv = b[e], pv = p[e], ppv = pp[e];
+        // t = b - conj(alpha) p - beta p'  (beta real)
+        cx<T> t = mk<T>(bv.x - (ax * pv.x + ay * pv.y) - bp * ppv.x,
+                        bv.y - (ax * pv.y - ay * pv.x) - bp * ppv.y);
+        pp[e] = t;
+        s0x += t.x * r.x + t.y * r.y;
+        s0y += t.x * r.y - t.y * r.x;
+        s1 += rn;
+        s2 += t.x * t.x + t.y * t.y;
+      } else {
+        s0x += e >= half ? -rn : rn;
+        s1 += rn;
+      }
     }
+    acc[0].x += (double)s0x;
+    acc[0].y += (double)s0y;
+    acc[1].x += (double)s1;
+    acc[2].x += (double)s2;
   }
   block_sum_store<4>(acc, partial);
 }
@@ -334,146 +356,193 @@ template void jflip_copy<double>(Context &, QSlot &, const double2 *, double2 *)
 template void jflip_copy<float>(Context &, QSlot &, const float2 *, float2 *);
 
 // ================================================================== chains
+// Chains on the same q-slot form a group whose vectors are stacked so that one
+// Liouvillian pass serves them all (the occupied orbitals are read once per pass).
+// Vector slots of a group (m members; each slot holds a block of vectors):
+//   NH : 0 [q_1..q_m, p_1..p_m]  1 [q'.., p'..]  2 [a.., b..]   (L on q, L^H on p)
+//   PH : 0 [q..]  1 [q'..]  2 [a..]
+//   PHM: 0 [q..]  1 [q'.. / r..]  2 [Lq..]  3 [w..]
 template <class T>
 void ChainSet::init_impl() {
-  size_t c = sizeof(cx<T>);
+  const size_t c = sizeof(cx<T>);
   red.alloc((size_t)kRedBlocks * 4 * sizeof(double2));
-  for (auto &ch : chains) {
-    QSlot &s = *ctx->slots[ch.qslot];
+  for (size_t i = 0; i < chains.size(); ++i) {
+    Chain &ch = chains[i];
+    int g = -1;
+    for (size_t j = 0; j < groups.size(); ++j)
+      if (groups[j].qslot == ch.qslot) g = (int)j;
+    if (g < 0) {
+      groups.push_back(Group{});
+      g = (int)groups.size() - 1;
+      groups[g].qslot = ch.qslot;
+    }
+    ch.group = g;
+    ch.index = (int)groups[g].members.size();
+    groups[g].members.push_back((int)i);
+  }
+  for (Group &gr : groups) {
+    QSlot &s = *ctx->slots[gr.qslot];
     ensure_precision<T>(*ctx, s);
-    long long n = s.br_elems();
-    int nvec = flavor == TDLZ_NONHERMITIAN ? 6 : 4;
-    ch.vec.alloc((size_t)nvec * n * c);
-    TDLZ_CUDA_TRY(cudaMemsetAsync(ch.vec.p, 0, ch.vec.bytes, ctx->stream));
-    for (int i = 0; i < nvec; ++i) ch.v[i] = (char *)ch.vec.p + (size_t)i * n * c;
-    ch.coef.alloc((size_t)cap * (sizeof(double2) * 5 + sizeof(double)));
-    TDLZ_CUDA_TRY(cudaMemsetAsync(ch.coef.p, 0, ch.coef.bytes, ctx->stream));
-    ch.cf.cap = cap;
-    ch.cf.alpha = ch.coef.as<double2>();
-    ch.cf.gamma = ch.cf.alpha + cap;
-    ch.cf.z = ch.cf.gamma + cap;
-    ch.cf.beta = reinterpret_cast<double *>(ch.cf.z + 3 * (size_t)cap);
-    ch.sc.alloc(sizeof(ChainScalars));
-    TDLZ_CUDA_TRY(cudaMemsetAsync(ch.sc.p, 0, ch.sc.bytes, ctx->stream));
-    // start vector into Q (slot 0)
-    cx<T> *Q = (cx<T> *)ch.v[0];
-    start_vector<T>(*ctx, s, ch.mu, Q);
+    const long long n = s.br_elems(), half = n / 2;
+    const int m = (int)gr.members.size();
+    gr.nv = flavor == TDLZ_NONHERMITIAN ? 2 * m : m;
+    const int nslot = flavor == TDLZ_PSEUDOHERMITIAN_POSDEF ? 4 : 3;
+    gr.vec.alloc((size_t)nslot * gr.nv * n * c);
+    TDLZ_CUDA_TRY(cudaMemsetAsync(gr.vec.p, 0, gr.vec.bytes, ctx->stream));
+    for (int k = 0; k < nslot; ++k) gr.slot[k] = (char *)gr.vec.p + (size_t)k * gr.nv * n * c;
+    for (int mi = 0; mi < m; ++mi) {
+      Chain &ch = chains[gr.members[mi]];
+      ch.coef.alloc((size_t)cap * (sizeof(double2) * 5 + sizeof(double)));
+      TDLZ_CUDA_TRY(cudaMemsetAsync(ch.coef.p, 0, ch.coef.bytes, ctx->stream));
+      ch.cf.cap = cap;
+      ch.cf.alpha = ch.coef.as<double2>();
+      ch.cf.gamma = ch.cf.alpha + cap;
+      ch.cf.z = ch.cf.gamma + cap;
+      ch.cf.beta = reinterpret_cast<double *>(ch.cf.z + 3 * (size_t)cap);
+      ch.sc.alloc(sizeof(ChainScalars));
+      TDLZ_CUDA_TRY(cudaMemsetAsync(ch.sc.p, 0, ch.sc.bytes, ctx->stream));
+      start_vector<T>(*ctx, s, ch.mu, (cx<T> *)gr.slot[0] + mi * n);
+    }
+    if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF)  // w = L v for every member, one pass
+      apply_liouvillian<T>(*ctx, s, (cx<T> *)gr.slot[0], (cx<T> *)gr.slot[3], m, 0u);
     double2 *part = red.as<double2>();
-    ChainScalars *cs = ch.sc.as<ChainScalars>();
-    long long half = n / 2;
-    Pairs pr{};
-    if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) {
-      // v in Q; W = L v in slot 3; c0 = v^H J W
-      cx<T> *W = (cx<T> *)ch.v[3];
-      apply_liouvillian<T>(*ctx, s, Q, W, false);
+    for (int mi = 0; mi < m; ++mi) {
+      Chain &ch = chains[gr.members[mi]];
+      ChainScalars *cs = ch.sc.as<ChainScalars>();
+      cx<T> *Q = (cx<T> *)gr.slot[0] + mi * n;
+      Pairs pr{};
       pr.n = 1;
-      pr.p[0] = Pair{Q, W, 1};
-    } else {
-      pr.n = 1;
-      pr.p[0] = Pair{Q, Q, flavor == TDLZ_PSEUDOHERMITIAN ? 1 : 0};
-    }
-    launch_dots<T>(*ctx, pr, n, half, part);
-    scalar_init_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, flavor);
-    TDLZ_LAUNCH_CHECK();
-    scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(Q, &cs->scale_q, n);
-    TDLZ_LAUNCH_CHECK();
-    if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) {
-      // Lq = W / n0 lives in slot 2
-      std::swap(ch.v[2], ch.v[3]);
-      scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>((cx<T> *)ch.v[2], &cs->scale_q, n);
+      if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF)
+        pr.p[0] = Pair{Q, (cx<T> *)gr.slot[3] + mi * n, 1};
+      else
+        pr.p[0] = Pair{Q, Q, flavor == TDLZ_PSEUDOHERMITIAN ? 1 : 0};
+      launch_dots<T>(*ctx, pr, n, half, part);
+      scalar_init_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, flavor);
       TDLZ_LAUNCH_CHECK();
+      scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(Q, &cs->scale_q, n);
+      TDLZ_LAUNCH_CHECK();
+      if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) {
+        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>((cx<T> *)gr.slot[3] + mi * n,
+                                                                &cs->scale_q, n);
+        TDLZ_LAUNCH_CHECK();
+      }
+      if (flavor == TDLZ_NONHERMITIAN)  // p_1 = q_1
+        TDLZ_CUDA_TRY(cudaMemcpyAsync((cx<T> *)gr.slot[0] + (m + mi) * n, Q, n * c,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
     }
-    if (flavor == TDLZ_NONHERMITIAN) {
-      // P = Q
-      TDLZ_CUDA_TRY(cudaMemcpyAsync(ch.v[3], Q, n * c, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
+    if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) std::swap(gr.slot[2], gr.slot[3]);  // Lq = w / n0
   }
 }
 
-// Vector slots:  NH: 0 q, 1 q', 2 a, 3 p, 4 p', 5 b
-//                PH: 0 q, 1 q', 2 a
-//                PHM: 0 q, 1 q' (r), 2 Lq, 3 w
 template <class T>
 void ChainSet::advance_impl(int nsteps) {
-  for (auto &ch : chains) {
-    QSlot &s = *ctx->slots[ch.qslot];
-    long long n = s.br_elems(), half = n / 2;
-    double2 *part = red.as<double2>();
-    ChainScalars *cs = ch.sc.as<ChainScalars>();
-    SlotData<T> &d = slot_data<T>(s);
-    const cx<T> *u = d.uvec.template as<cx<T>>();
-    for (int it = 0; it < nsteps; ++it) {
-      if (ch.host_step >= cap) break;
-      cx<T> *Q = (cx<T> *)ch.v[0], *QP = (cx<T> *)ch.v[1], *A = (cx<T> *)ch.v[2];
-      Pairs pr{};
-      pr.n = 4;
+  double2 *part = red.as<double2>();
+  for (int it = 0; it < nsteps; ++it) {
+    for (Group &gr : groups) {
+      if (gr.host_step >= cap) continue;
+      QSlot &s = *ctx->slots[gr.qslot];
+      const long long n = s.br_elems(), half = n / 2;
+      const int m = (int)gr.members.size();
+      const cx<T> *u = slot_data<T>(s).uvec.template as<cx<T>>();
+      cx<T> *S0 = (cx<T> *)gr.slot[0], *S1 = (cx<T> *)gr.slot[1], *S2 = (cx<T> *)gr.slot[2];
       if (flavor == TDLZ_NONHERMITIAN) {
-        cx<T> *P = (cx<T> *)ch.v[3], *PP = (cx<T> *)ch.v[4], *B = (cx<T> *)ch.v[5];
-        apply_liouvillian<T>(*ctx, s, Q, A, false);
-        apply_liouvillian<T>(*ctx, s, P, B, true);
-        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 20.0 * n * sizeof(cx<T>), 40.0 * n);
-        pr.p[0] = Pair{P, A, 0};
-        for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
-        launch_dots<T>(*ctx, pr, n, half, part);
-        scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
-        TDLZ_LAUNCH_CHECK();
-        update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(A, Q, QP, B, P, PP, cs, flavor,
-                                                                     n, half, part);
-        TDLZ_LAUNCH_CHECK();
-        scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
-        TDLZ_LAUNCH_CHECK();
-        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
-        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(PP, &cs->scale_p, n);
-        TDLZ_LAUNCH_CHECK();
-        std::swap(ch.v[0], ch.v[1]);
-        std::swap(ch.v[3], ch.v[4]);
+        // a = L q and b = L^H p for every member in one pass
+        const unsigned mask = ((1u << m) - 1u) << m;  // m <= 16 (checked at creation)
+        apply_liouvillian<T>(*ctx, s, S0, S2, 2 * m, mask);
+        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 20.0 * m * n * sizeof(cx<T>),
+                     40.0 * m * n);
+        for (int mi = 0; mi < m; ++mi) {
+          Chain &ch = chains[gr.members[mi]];
+          ChainScalars *cs = ch.sc.as<ChainScalars>();
+          cx<T> *Q = S0 + mi * n, *P = S0 + (m + mi) * n, *QP = S1 + mi * n,
+                *PP = S1 + (m + mi) * n, *A = S2 + mi * n, *B = S2 + (m + mi) * n;
+          Pairs pr{};
+          pr.n = 4;
+          pr.p[0] = Pair{P, A, 0};
+          for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
+          launch_dots<T>(*ctx, pr, n, half, part);
+          scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          TDLZ_LAUNCH_CHECK();
+          update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(A, Q, QP, B, P, PP, cs,
+                                                                       flavor, n, half, part);
+          TDLZ_LAUNCH_CHECK();
+          scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          TDLZ_LAUNCH_CHECK();
+          scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
+          scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(PP, &cs->scale_p, n);
+          TDLZ_LAUNCH_CHECK();
+        }
+        std::swap(gr.slot[0], gr.slot[1]);
       } else if (flavor == TDLZ_PSEUDOHERMITIAN) {
-        apply_liouvillian<T>(*ctx, s, Q, A, false);
-        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 11.0 * n * sizeof(cx<T>), 28.0 * n);
-        pr.p[0] = Pair{Q, A, 1};
-        for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
-        launch_dots<T>(*ctx, pr, n, half, part);
-        scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
-        TDLZ_LAUNCH_CHECK();
-        update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
-            A, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
-        TDLZ_LAUNCH_CHECK();
-        scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
-        TDLZ_LAUNCH_CHECK();
-        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
-        TDLZ_LAUNCH_CHECK();
-        std::swap(ch.v[0], ch.v[1]);
-      } else {
-        cx<T> *LQ = A, *W = (cx<T> *)ch.v[3];
-        {
-          ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 9.0 * n * sizeof(cx<T>), 24.0 * n);
-          pr.p[0] = Pair{LQ, LQ, 1};
+        apply_liouvillian<T>(*ctx, s, S0, S2, m, 0u);
+        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 11.0 * m * n * sizeof(cx<T>),
+                     28.0 * m * n);
+        for (int mi = 0; mi < m; ++mi) {
+          Chain &ch = chains[gr.members[mi]];
+          ChainScalars *cs = ch.sc.as<ChainScalars>();
+          cx<T> *Q = S0 + mi * n, *QP = S1 + mi * n, *A = S2 + mi * n;
+          Pairs pr{};
+          pr.n = 4;
+          pr.p[0] = Pair{Q, A, 1};
           for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
           launch_dots<T>(*ctx, pr, n, half, part);
           scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
           TDLZ_LAUNCH_CHECK();
           update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
-              LQ, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
+              A, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
+          TDLZ_LAUNCH_CHECK();
+          scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          TDLZ_LAUNCH_CHECK();
+          scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
           TDLZ_LAUNCH_CHECK();
         }
-        apply_liouvillian<T>(*ctx, s, QP, W, false);
-        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 6.0 * n * sizeof(cx<T>), 12.0 * n);
-        Pairs pc{};
-        pc.n = 3;
-        pc.p[0] = Pair{QP, W, 1};
-        pc.p[1] = Pair{QP, QP, 0};
-        pc.p[2] = Pair{W, W, 0};
-        launch_dots<T>(*ctx, pc, n, half, part);
-        scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
-        TDLZ_LAUNCH_CHECK();
-        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
-        scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(W, &cs->scale_q, n);
-        TDLZ_LAUNCH_CHECK();
+        std::swap(gr.slot[0], gr.slot[1]);
+      } else {
+        cx<T> *S3 = (cx<T> *)gr.slot[3];
+        {
+          ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 9.0 * m * n * sizeof(cx<T>),
+                       24.0 * m * n);
+          for (int mi = 0; mi < m; ++mi) {
+            Chain &ch = chains[gr.members[mi]];
+            ChainScalars *cs = ch.sc.as<ChainScalars>();
+            cx<T> *Q = S0 + mi * n, *QP = S1 + mi * n, *LQ = S2 + mi * n;
+            Pairs pr{};
+            pr.n = 4;
+            pr.p[0] = Pair{LQ, LQ, 1};
+            for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
+            launch_dots<T>(*ctx, pr, n, half, part);
+            scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf,
+                                                                flavor);
+            TDLZ_LAUNCH_CHECK();
+            update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
+                LQ, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
+            TDLZ_LAUNCH_CHECK();
+          }
+        }
+        apply_liouvillian<T>(*ctx, s, S1, S3, m, 0u);  // w = L r for every member
+        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 6.0 * m * n * sizeof(cx<T>),
+                     12.0 * m * n);
+        for (int mi = 0; mi < m; ++mi) {
+          Chain &ch = chains[gr.members[mi]];
+          ChainScalars *cs = ch.sc.as<ChainScalars>();
+          cx<T> *QP = S1 + mi * n, *W = S3 + mi * n;
+          Pairs pc{};
+          pc.n = 3;
+          pc.p[0] = Pair{QP, W, 1};
+          pc.p[1] = Pair{QP, QP, 0};
+          pc.p[2] = Pair{W, W, 0};
+          launch_dots<T>(*ctx, pc, n, half, part);
+          scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          TDLZ_LAUNCH_CHECK();
+          scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(QP, &cs->scale_q, n);
+          scale_kernel<T><<<blocks_for(n), 256, 0, ctx->stream>>>(W, &cs->scale_q, n);
+          TDLZ_LAUNCH_CHECK();
+        }
         // q' <- q, q <- r/beta, Lq <- w/beta, w <- old Lq
-        std::swap(ch.v[0], ch.v[1]);
-        std::swap(ch.v[2], ch.v[3]);
+        std::swap(gr.slot[0], gr.slot[1]);
+        std::swap(gr.slot[2], gr.slot[3]);
       }
-      ch.host_step++;
+      gr.host_step++;
     }
   }
 }
@@ -530,6 +599,128 @@ void ChainSet::read(tdlz_lanczos_result *res) {
     if (res->wk) res->wk[c] = ctx->slots[ch.qslot]->wk[0];
     if (res->steps_done) res->steps_done[c] = done;
     if (res->status) res->status[c] = hs.status;
+  }
+}
+
+// ================================================================ restart
+// Image: RestartHeader, then per chain (qslot, mu), per group host_step, then for
+// each group its vector slots in logical order, then per chain ChainScalars and
+// the coefficient block (cap entries).  A chain set created with the same
+// chains, flavour and precision and a capacity >= the saved one accepts it.
+namespace {
+struct RestartHeader {
+  char magic[8];
+  int version, flavor, precision, nchain, ngroup, cap;
+};
+size_t vec_elem_bytes(int precision) { return precision == TDLZ_FP64 ? 16 : 8; }
+int nslots(int flavor) { return flavor == TDLZ_PSEUDOHERMITIAN_POSDEF ? 4 : 3; }
+}  // namespace
+
+size_t ChainSet::state_bytes() const {
+  size_t b = sizeof(RestartHeader) + chains.size() * 2 * sizeof(int) + groups.size() * sizeof(int);
+  for (const Group &g : groups) {
+    const QSlot &s = *ctx->slots[g.qslot];
+    b += (size_t)nslots(flavor) * g.nv * s.br_elems() * vec_elem_bytes(precision);
+  }
+  b += chains.size() * (sizeof(ChainScalars) + (size_t)cap * (5 * sizeof(double2) + sizeof(double)));
+  return b;
+}
+
+void ChainSet::save(void *host, size_t bytes) {
+  TDLZ_REQUIRE(bytes >= state_bytes(), TDLZ_ERR_ARG, "restart buffer too small");
+  TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  char *p = static_cast<char *>(host);
+  RestartHeader h{};
+  std::memcpy(h.magic, "TDLZRST", 8);
+  h.version = 1;
+  h.flavor = flavor;
+  h.precision = precision;
+  h.nchain = (int)chains.size();
+  h.ngroup = (int)groups.size();
+  h.cap = cap;
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (const Chain &c : chains) {
+    int qm[2] = {c.qslot, c.mu};
+    std::memcpy(p, qm, sizeof(qm));
+    p += sizeof(qm);
+  }
+  for (const Group &g : groups) {
+    std::memcpy(p, &g.host_step, sizeof(int));
+    p += sizeof(int);
+  }
+  for (const Group &g : groups) {
+    const QSlot &s = *ctx->slots[g.qslot];
+    size_t sb = (size_t)g.nv * s.br_elems() * vec_elem_bytes(precision);
+    for (int k = 0; k < nslots(flavor); ++k) {
+      TDLZ_CUDA_TRY(cudaMemcpy(p, g.slot[k], sb, cudaMemcpyDeviceToHost));
+      p += sb;
+    }
+  }
+  const size_t cb = (size_t)cap * (5 * sizeof(double2) + sizeof(double));
+  for (const Chain &c : chains) {
+    TDLZ_CUDA_TRY(cudaMemcpy(p, c.sc.p, sizeof(ChainScalars), cudaMemcpyDeviceToHost));
+    p += sizeof(ChainScalars);
+    TDLZ_CUDA_TRY(cudaMemcpy(p, c.coef.p, cb, cudaMemcpyDeviceToHost));
+    p += cb;
+  }
+}
+
+void ChainSet::restore(const void *host, size_t bytes) {
+  const char *p = static_cast<const char *>(host);
+  TDLZ_REQUIRE(bytes >= sizeof(RestartHeader), TDLZ_ERR_ARG, "restart image truncated");
+  RestartHeader h;
+  std::memcpy(&h, p, sizeof(h));
+  p += sizeof(h);
+  TDLZ_REQUIRE(std::memcmp(h.magic, "TDLZRST", 8) == 0 && h.version == 1, TDLZ_ERR_ARG,
+               "not a tdlz restart image");
+  TDLZ_REQUIRE(h.flavor == flavor && h.precision == precision && h.nchain == (int)chains.size() &&
+                   h.ngroup == (int)groups.size(),
+               TDLZ_ERR_ARG, "restart image was saved from a different chain set");
+  TDLZ_REQUIRE(h.cap <= cap, TDLZ_ERR_ARG, "restart image holds more steps than this capacity");
+  for (const Chain &c : chains) {
+    int qm[2];
+    std::memcpy(qm, p, sizeof(qm));
+    p += sizeof(qm);
+    TDLZ_REQUIRE(qm[0] == c.qslot && qm[1] == c.mu, TDLZ_ERR_ARG,
+                 "restart image chains differ (q-slot or mu)");
+  }
+  size_t need = sizeof(RestartHeader) + chains.size() * 2 * sizeof(int) + groups.size() * sizeof(int);
+  for (const Group &g : groups)
+    need += (size_t)nslots(flavor) * g.nv * ctx->slots[g.qslot]->br_elems() *
+            vec_elem_bytes(precision);
+  const size_t cb_old = (size_t)h.cap * (5 * sizeof(double2) + sizeof(double));
+  need += chains.size() * (sizeof(ChainScalars) + cb_old);
+  TDLZ_REQUIRE(bytes >= need, TDLZ_ERR_ARG, "restart image truncated");
+  std::vector<int> steps(groups.size());
+  for (size_t i = 0; i < groups.size(); ++i) {
+    std::memcpy(&steps[i], p, sizeof(int));
+    p += sizeof(int);
+  }
+  TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (size_t i = 0; i < groups.size(); ++i) {
+    Group &g = groups[i];
+    size_t sb = (size_t)g.nv * ctx->slots[g.qslot]->br_elems() * vec_elem_bytes(precision);
+    for (int k = 0; k < nslots(flavor); ++k) {
+      TDLZ_CUDA_TRY(cudaMemcpy(g.slot[k], p, sb, cudaMemcpyHostToDevice));
+      p += sb;
+    }
+    g.host_step = steps[i];
+  }
+  for (Chain &c : chains) {
+    TDLZ_CUDA_TRY(cudaMemcpy(c.sc.p, p, sizeof(ChainScalars), cudaMemcpyHostToDevice));
+    p += sizeof(ChainScalars);
+    // coefficient block [alpha cap][gamma cap][z 3 cap][beta cap]: copy each part
+    const double2 *src = reinterpret_cast<const double2 *>(p);
+    TDLZ_CUDA_TRY(cudaMemcpy(c.cf.alpha, src, h.cap * sizeof(double2), cudaMemcpyHostToDevice));
+    TDLZ_CUDA_TRY(cudaMemcpy(c.cf.gamma, src + h.cap, h.cap * sizeof(double2),
+                             cudaMemcpyHostToDevice));
+    for (int l = 0; l < 3; ++l)
+      TDLZ_CUDA_TRY(cudaMemcpy(c.cf.z + (size_t)l * cap, src + (size_t)(2 + l) * h.cap,
+                               h.cap * sizeof(double2), cudaMemcpyHostToDevice));
+    TDLZ_CUDA_TRY(cudaMemcpy(c.cf.beta, reinterpret_cast<const double *>(src + 5 * (size_t)h.cap),
+                             h.cap * sizeof(double), cudaMemcpyHostToDevice));
+    p += cb_old;
   }
 }
 

@@ -25,9 +25,18 @@ struct ChainCoeffs {
 
 struct Chain {
   int qslot = 0, mu = 0;
-  DevBuf vec, coef, sc;
-  void *v[6] = {nullptr};
+  int group = -1, index = 0;  // its group and position in the group's vector blocks
+  DevBuf coef, sc;
   ChainCoeffs cf{};
+};
+
+// Chains on one q-slot: their vectors are stacked so one Liouvillian pass serves all.
+struct Group {
+  int qslot = 0;
+  std::vector<int> members;
+  int nv = 0;  // vectors per slot block (2 x members for NH)
+  DevBuf vec;
+  void *slot[4] = {nullptr, nullptr, nullptr, nullptr};
   int host_step = 0;
 };
 
@@ -35,10 +44,16 @@ struct ChainSet {
   Context *ctx = nullptr;
   int flavor = 0, precision = 0, cap = 0;
   std::vector<Chain> chains;
+  std::vector<Group> groups;
   DevBuf red;
   void init();
   void advance(int nsteps);
   void read(tdlz_lanczos_result *res);
+  // restart image: header, each group's vector slots in logical order, each
+  // chain's device scalars and coefficients
+  size_t state_bytes() const;
+  void save(void *host, size_t bytes);
+  void restore(const void *host, size_t bytes);
 
  private:
   template <class T> void init_impl();

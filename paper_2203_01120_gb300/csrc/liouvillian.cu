@@ -18,6 +18,7 @@
 #include <unordered_map>
 
 #include "engine.cuh"
+#include "pipeline.cuh"
 
 namespace tdlz {
 
@@ -40,30 +41,6 @@ __global__ void scatter_rows_kernel(const cx<T> *__restrict__ x, cx<T> *__restri
   }
 }
 
-// h = scale * grid[G] + (kin - e_n) x  on the k+q sphere; zero padding.
-template <class T>
-__global__ void gather_rows_kernel(const cx<T> *__restrict__ grid, const cx<T> *__restrict__ x,
-                                   cx<T> *__restrict__ h, const int *__restrict__ idx,
-                                   const T *__restrict__ kin, const T *__restrict__ evals, int nk,
-                                   int nb, int npwx, long long nr, T scale, long long nrows) {
-  long long row = blockIdx.y + (long long)gridDim.y * blockIdx.z;
-  if (row >= nrows) return;
-  long long band = row / 2;  // (side, k, n)
-  int k = (int)((band / nb) % nk);
-  T e = evals[band];
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npwx; g += gridDim.x * blockDim.x) {
-    int ig = idx[(long long)k * npwx + g];
-    cx<T> out = czero<T>();
-    if (ig >= 0) {
-      cx<T> gv = grid[row * nr + ig];
-      cx<T> xv = x[row * npwx + g];
-      T d = kin[(long long)k * npwx + g] - e;
-      out = mk<T>(gv.x * scale + d * xv.x, gv.y * scale + d * xv.y);
-    }
-    h[row * npwx + g] = out;
-  }
-}
-
 inline dim3 row_grid(long long nrows, int npwx) {
   unsigned bx = (unsigned)((npwx + kThreads - 1) / kThreads);
   long long y = nrows, z = 1;
@@ -77,38 +54,102 @@ inline dim3 row_grid(long long nrows, int npwx) {
 // ------------------------------------------------------------- density (a3)
 // rho'_a(r) = sum_k w_k sum_n [ U^X_n^+ s_a x_n + t_a U^Y_n^+ s_a y_n ],
 // t = (1,-1,-1,-1); fixed summation order (deterministic).
-template <class T>
+// nvec response vectors share the occupied orbitals: each U(r) value is read once
+// and contracted with every vector's x(r); rho is [nvec][4][Nr].
+// Block row y sums the (side, k) pairs [y*ppg, (y+1)*ppg) into partial slice y
+// ([gridDim.y][nvec][4][Nr]); density_reduce_kernel adds the slices in order.
+template <class T, int NV>
 __global__ void density_kernel(const cx<T> *__restrict__ ur, const cx<T> *__restrict__ xr,
                                const T *__restrict__ wk, cx<T> *__restrict__ rho, int nk, int nb,
-                               long long nr) {
+                               long long nr, int nvec, int ppg, int vstride) {
+  const long long rows1 = 4LL * nk * nb;
+  const int pb = blockIdx.y * ppg, pe = min(2 * nk, pb + ppg);
+  rho += (long long)blockIdx.y * vstride * 4 * nr;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
        r += (long long)gridDim.x * blockDim.x) {
-    cx<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-    for (int side = 0; side < 2; ++side) {
+    cx<T> acc[NV][4];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      for (int a = 0; a < 4; ++a) acc[v][a] = czero<T>();
+    for (int pair = pb; pair < pe; ++pair) {
+      const int side = pair / nk, k = pair - side * nk;
       T t = side == 0 ? T(1) : T(-1);
-      for (int k = 0; k < nk; ++k) {
-        cx<T> a0 = czero<T>(), a1 = czero<T>(), a2 = czero<T>(), a3 = czero<T>();
+      {
+        cx<T> a[NV][4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          for (int c = 0; c < 4; ++c) a[v][c] = czero<T>();
         for (int n = 0; n < nb; ++n) {
           long long row = (((long long)side * nk + k) * nb + n) * 2;
           cx<T> u0 = ur[row * nr + r], u1 = ur[(row + 1) * nr + r];
-          cx<T> x0 = xr[row * nr + r], x1 = xr[(row + 1) * nr + r];
-          cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
-          cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
-          a0 = cadd<T>(a0, cadd<T>(p00, p11));
-          a1 = cadd<T>(a1, cadd<T>(p01, p10));
-          cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
-          a2 = cadd<T>(a2, mk<T>(-d.y, d.x));
-          a3 = cadd<T>(a3, csub<T>(p00, p11));
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            if (v >= nvec) break;
+            long long rv = row + v * rows1;
+            cx<T> x0 = xr[rv * nr + r], x1 = xr[(rv + 1) * nr + r];
+            cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
+            cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
+            a[v][0] = cadd<T>(a[v][0], cadd<T>(p00, p11));
+            a[v][1] = cadd<T>(a[v][1], cadd<T>(p01, p10));
+            cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
+            a[v][2] = cadd<T>(a[v][2], mk<T>(-d.y, d.x));
+            a[v][3] = cadd<T>(a[v][3], csub<T>(p00, p11));
+          }
         }
         T w = wk[k];
-        acc[0] = cadd<T>(acc[0], cscale<T>(a0, w));
-        acc[1] = cadd<T>(acc[1], cscale<T>(a1, w * t));
-        acc[2] = cadd<T>(acc[2], cscale<T>(a2, w * t));
-        acc[3] = cadd<T>(acc[3], cscale<T>(a3, w * t));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          acc[v][0] = cadd<T>(acc[v][0], cscale<T>(a[v][0], w));
+          for (int c = 1; c < 4; ++c) acc[v][c] = cadd<T>(acc[v][c], cscale<T>(a[v][c], w * t));
+        }
       }
     }
-    for (int a = 0; a < 4; ++a) rho[a * nr + r] = acc[a];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v >= nvec) break;
+      for (int a = 0; a < 4; ++a) rho[((long long)v * 4 + a) * nr + r] = acc[v][a];
+    }
   }
+}
+
+// rho[v][a][r] = sum_g part[g][v][a][r] in fixed order
+template <class T>
+__global__ void density_reduce_kernel(const cx<T> *__restrict__ part, cx<T> *__restrict__ rho,
+                                      int ngroup, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cx<T> s = part[i];
+    for (int g = 1; g < ngroup; ++g) s = cadd<T>(s, part[(long long)g * n + i]);
+    rho[i] = s;
+  }
+}
+
+constexpr int kDensityGroups = 8;
+
+template <class T>
+void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *wk, cx<T> *rho,
+                    cx<T> *part, int nk, int nb, long long nr, int nvec) {
+  // (side, k) pairs split over kDensityGroups block rows for parallelism; up to 3
+  // vectors per pass (register budget), each sharing the U(r) reads
+  const long long rows1 = 4LL * nk * nb;
+  const int npair = 2 * nk;
+  const int ngroup = std::min(kDensityGroups, npair);
+  const int ppg = (npair + ngroup - 1) / ngroup;
+  const int ng = (npair + ppg - 1) / ppg;
+  const dim3 grid(blocks_for(nr), ng);
+  for (int v0 = 0; v0 < nvec; v0 += 3) {
+    int nv = std::min(3, nvec - v0);
+    const cx<T> *xv = xr + (long long)v0 * rows1 * nr;
+    cx<T> *pv = part + (long long)v0 * 4 * nr;
+    if (nv == 1)
+      density_kernel<T, 1><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, 1, ppg, nvec);
+    else
+      density_kernel<T, 3><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, nv, ppg, nvec);
+    TDLZ_LAUNCH_CHECK();
+  }
+  long long n = (long long)nvec * 4 * nr;
+  density_reduce_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(part, rho, ng, n);
+  TDLZ_LAUNCH_CHECK();
 }
 
 // --------------------------------------------------------- Hartree + ALSDA
@@ -158,66 +199,36 @@ __global__ void potential_kernel(const cx<T> *__restrict__ rho, const cx<T> *__r
   }
 }
 
-// -------------------------------------------------------- products (a6)
-// t = [v_loc + s B.sigma] x + W^s U, in place over x(r); W^s = v0 + s v.sigma.
-template <class T>
-__global__ void product_kernel(cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
-                               const T *__restrict__ vloc, const T *__restrict__ bf,
-                               const cx<T> *__restrict__ v, int nk, int nb, long long nr,
-                               long long nbs) {
-  long long bs = blockIdx.y + (long long)gridDim.y * blockIdx.z;  // band-side (side,k,n)
-  if (bs >= nbs) return;
-  int side = (int)(bs / ((long long)nk * nb));
-  T s = side == 0 ? T(1) : T(-1);
-  long long row = bs * 2;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
-       r += (long long)gridDim.x * blockDim.x) {
-    T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
-    cx<T> v0 = v[r], v1 = v[nr + r], v2 = v[2 * nr + r], v3 = v[3 * nr + r];
-    cx<T> x0 = xr[row * nr + r], x1 = xr[(row + 1) * nr + r];
-    cx<T> u0 = ur[row * nr + r], u1 = ur[(row + 1) * nr + r];
-    // ground local 2x2: [[vl + s bz, s(bx - i by)], [s(bx + i by), vl - s bz]]
-    cx<T> h01 = mk<T>(s * bx, -s * by), h10 = mk<T>(s * bx, s * by);
-    cx<T> t0 = cscale<T>(x0, vl + s * bz);
-    cfma<T>(t0, h01, x1);
-    cx<T> t1 = cscale<T>(x1, vl - s * bz);
-    cfma<T>(t1, h10, x0);
-    // W^s: [[v0 + s v3, s(v1 - i v2)], [s(v1 + i v2), v0 - s v3]]
-    cx<T> w00 = mk<T>(v0.x + s * v3.x, v0.y + s * v3.y);
-    cx<T> w11 = mk<T>(v0.x - s * v3.x, v0.y - s * v3.y);
-    cx<T> w01 = mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x));
-    cx<T> w10 = mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x));
-    cfma<T>(t0, w00, u0);
-    cfma<T>(t0, w01, u1);
-    cfma<T>(t1, w10, u0);
-    cfma<T>(t1, w11, u1);
-    xr[row * nr + r] = t0;
-    xr[(row + 1) * nr + r] = t1;
-  }
-}
-
 // ------------------------------------------------------------------ GEMMs
 // Split-K reduction GEMM: part[z][b][m][n] = sum_{k in split z} conj(A[bA][m][k]) B[b][n][k].
-constexpr int TM = 32, TN = 32, KC = 16;
-template <class T>
+// 16 x 16 threads, each holding an R x R register tile (rows ty + 16 i, columns
+// tx + 16 j), so one CTA covers a (16 R) x (16 R) output tile: per shared-memory
+// load a thread does R complex multiply-adds.
+constexpr int KC = 16;
+template <class T, int R>
 __global__ void __launch_bounds__(256)
     gemm_tn_kernel(const cx<T> *__restrict__ A, long long lda, long long sA, int amod,
                    const cx<T> *__restrict__ B, long long ldb, long long sB,
                    cx<T> *__restrict__ part, int M, int N, long long K, int batch, int nsplit) {
-  __shared__ cx<T> As[TM][KC + 1];
-  __shared__ cx<T> Bs[TN][KC + 1];
+  constexpr int TT = 16 * R;
+  __shared__ cx<T> As[TT][KC + 1];
+  __shared__ cx<T> Bs[TT][KC + 1];
   int z = blockIdx.z;
   int b = z % batch;
   int sp = z / batch;
-  int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  int m0 = blockIdx.y * TT, n0 = blockIdx.x * TT;
   long long kchunk = (K + nsplit - 1) / nsplit;
   long long kb = sp * kchunk, ke = kb + kchunk < K ? kb + kchunk : K;
   const cx<T> *Ab = A + (long long)(b % amod) * sA;
   const cx<T> *Bb = B + (long long)b * sB;
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cx<T> acc[2][2] = {{czero<T>(), czero<T>()}, {czero<T>(), czero<T>()}};
+  cx<T> acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = czero<T>();
   for (long long k0 = kb; k0 < ke; k0 += KC) {
-    for (int e = threadIdx.x; e < TM * KC; e += blockDim.x) {
+    for (int e = threadIdx.x; e < TT * KC; e += blockDim.x) {
       int rr = e / KC, kk = e % KC;
       long long kg = k0 + kk;
       cx<T> av = czero<T>(), bv = czero<T>();
@@ -231,17 +242,22 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < KC; ++kk) {
-      cx<T> a0 = As[ty][kk], a1 = As[ty + 16][kk];
-      cx<T> b0 = Bs[tx][kk], b1 = Bs[tx + 16][kk];
-      cfmac<T>(acc[0][0], a0, b0);
-      cfmac<T>(acc[0][1], a0, b1);
-      cfmac<T>(acc[1][0], a1, b0);
-      cfmac<T>(acc[1][1], a1, b1);
+      cx<T> av[R], bv[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) av[i] = As[ty + 16 * i][kk];
+#pragma unroll
+      for (int j = 0; j < R; ++j) bv[j] = Bs[tx + 16 * j][kk];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) cfmac<T>(acc[i][j], av[i], bv[j]);
     }
     __syncthreads();
   }
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
       int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m < M && n < N)
         part[(((long long)sp * batch + b) * M + m) * N + n] = acc[i][j];
@@ -266,24 +282,26 @@ __global__ void split_reduce_kernel(const cx<T> *__restrict__ part, cx<T> *__res
 }
 
 // Out[b][row][col] = sgn_b (In[b][row][col] + alpha sum_k A(b,row,k) B[b % bmod][k][col])
-constexpr int NN_ROWS = 8, NN_COLS = 128, NN_KMAX = 256;
+constexpr int NN_ROWS = 16, NN_COLS = 128, NN_KMAX = 256;
+// grid: x = row chunk (fastest, so the CTAs that share a B column tile run together
+// and re-read it from L2), y = column chunk, z = batch; A chunk in dynamic smem.
 template <class T>
 __global__ void __launch_bounds__(NN_COLS)
     gemm_nn_kernel(const cx<T> *__restrict__ A, long long sA, long long sar, long long sak,
                    const cx<T> *__restrict__ B, long long ldb, long long sB, int bmod,
                    const cx<T> *In, cx<T> *Out, long long ldo, long long sO, int rows,
-                   long long ncol, int K, T alpha, int neg_from) {
-  __shared__ cx<T> As[NN_ROWS][NN_KMAX];
+                   long long ncol, int K, T alpha, int neg_from, int neg_mod) {
+  extern __shared__ unsigned char nn_smem[];
+  cx<T> *As = reinterpret_cast<cx<T> *>(nn_smem);  // [NN_ROWS][K]
   int b = blockIdx.z;
-  int r0 = blockIdx.y * NN_ROWS;
+  int r0 = blockIdx.x * NN_ROWS;
   const cx<T> *Ab = A + (long long)b * sA;
   for (int e = threadIdx.x; e < NN_ROWS * K; e += blockDim.x) {
     int rr = e / K, kk = e % K;
-    As[rr][kk] = (r0 + rr < rows) ? Ab[(long long)(r0 + rr) * sar + (long long)kk * sak]
-                                  : czero<T>();
+    As[e] = (r0 + rr < rows) ? Ab[(long long)(r0 + rr) * sar + (long long)kk * sak] : czero<T>();
   }
   __syncthreads();
-  long long col = (long long)blockIdx.x * NN_COLS + threadIdx.x;
+  long long col = (long long)blockIdx.y * NN_COLS + threadIdx.x;
   if (col >= ncol) return;
   const cx<T> *Bb = B + (long long)(b % bmod) * sB;
   cx<T> acc[NN_ROWS];
@@ -292,9 +310,9 @@ __global__ void __launch_bounds__(NN_COLS)
   for (int kk = 0; kk < K; ++kk) {
     cx<T> bv = Bb[(long long)kk * ldb + col];
 #pragma unroll
-    for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r][kk], bv);
+    for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r * K + kk], bv);
   }
-  T sg = b >= neg_from ? T(-1) : T(1);
+  T sg = (b % neg_mod) >= neg_from ? T(-1) : T(1);
 #pragma unroll
   for (int r = 0; r < NN_ROWS; ++r) {
     if (r0 + r >= rows) break;
@@ -330,15 +348,25 @@ template <class T>
 void gemm_tn(Context &ctx, DevBuf &partbuf, const cx<T> *A, long long lda, long long sA, int amod,
              const cx<T> *B, long long ldb, long long sB, cx<T> *C, long long sC, long long ldcm,
              long long ldcn, int M, int N, long long K, int batch) {
-  int nsplit = (int)((K + 1023) / 1024);
-  if (nsplit < 1) nsplit = 1;
-  if (nsplit > 32) nsplit = 32;
+  // register tile R (CTA tile 16 R) from the larger output dimension, at most 5 (80)
+  const int R = std::max(1, std::min(5, (std::max(M, N) + 15) / 16));
+  const int TT = 16 * R;
+  const int tiles = ((M + TT - 1) / TT) * ((N + TT - 1) / TT);
+  // enough CTAs to fill the GPU: split K so that batch * tiles * nsplit >= ~4 waves
+  long long want = (4LL * 152 + (long long)batch * tiles - 1) / ((long long)batch * tiles);
+  long long ns = std::min(want, (K + 255) / 256);
+  int nsplit = (int)std::max(1LL, std::min(ns, 32LL));
   size_t need = (size_t)nsplit * batch * M * N * sizeof(cx<T>);
   TDLZ_REQUIRE(need <= partbuf.bytes, TDLZ_ERR_STATE, "split-K scratch too small");
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, (unsigned)(batch * nsplit));
-  gemm_tn_kernel<T><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB,
-                                                   partbuf.template as<cx<T>>(), M, N, K, batch,
-                                                   nsplit);
+  dim3 grid((N + TT - 1) / TT, (M + TT - 1) / TT, (unsigned)(batch * nsplit));
+  cx<T> *pp = partbuf.template as<cx<T>>();
+  switch (R) {
+    case 1: gemm_tn_kernel<T, 1><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB, pp, M, N, K, batch, nsplit); break;
+    case 2: gemm_tn_kernel<T, 2><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB, pp, M, N, K, batch, nsplit); break;
+    case 3: gemm_tn_kernel<T, 3><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB, pp, M, N, K, batch, nsplit); break;
+    case 4: gemm_tn_kernel<T, 4><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB, pp, M, N, K, batch, nsplit); break;
+    default: gemm_tn_kernel<T, 5><<<grid, 256, 0, ctx.stream>>>(A, lda, sA, amod, B, ldb, sB, pp, M, N, K, batch, nsplit); break;
+  }
   TDLZ_LAUNCH_CHECK();
   long long tot = (long long)batch * M * N;
   split_reduce_kernel<T><<<blocks_for(tot), kThreads, 0, ctx.stream>>>(
@@ -350,11 +378,15 @@ template <class T>
 void gemm_nn(Context &ctx, const cx<T> *A, long long sA, long long sar, long long sak,
              const cx<T> *B, long long ldb, long long sB, int bmod, const cx<T> *In, cx<T> *Out,
              long long ldo, long long sO, int rows, long long ncol, int K, T alpha, int batch,
-             int neg_from) {
+             int neg_from, int neg_mod = 1 << 30) {
   TDLZ_REQUIRE(K <= NN_KMAX, TDLZ_ERR_ARG, "contraction length above 256 (nocc or nproj)");
-  dim3 grid((unsigned)((ncol + NN_COLS - 1) / NN_COLS), (rows + NN_ROWS - 1) / NN_ROWS, batch);
-  gemm_nn_kernel<T><<<grid, NN_COLS, 0, ctx.stream>>>(A, sA, sar, sak, B, ldb, sB, bmod, In, Out,
-                                                     ldo, sO, rows, ncol, K, alpha, neg_from);
+  dim3 grid((rows + NN_ROWS - 1) / NN_ROWS, (unsigned)((ncol + NN_COLS - 1) / NN_COLS), batch);
+  size_t sm = (size_t)NN_ROWS * K * sizeof(cx<T>);
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(gemm_nn_kernel<T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  gemm_nn_kernel<T><<<grid, NN_COLS, sm, ctx.stream>>>(A, sA, sar, sak, B, ldb, sB, bmod, In, Out,
+                                                     ldo, sO, rows, ncol, K, alpha, neg_from,
+                                                     neg_mod);
   TDLZ_LAUNCH_CHECK();
 }
 
@@ -458,24 +490,49 @@ __global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restri
 
 
 template <class T>
-void alloc_workspace(QSlot &s) {
+void alloc_workspace(QSlot &s, int nvec) {
   Workspace<T> &w = slot_ws<T>(s);
-  if (w.ready) return;
-  size_t c = sizeof(cx<T>);
-  w.xr.alloc((size_t)s.rows() * s.nr * c);
-  w.rho.alloc(4 * (size_t)s.nr * c);
-  w.vpot.alloc(4 * (size_t)s.nr * c);
-  w.hgrid.alloc((size_t)s.nr * c);
-  w.h.alloc((size_t)s.br_elems() * c);
-  w.xin.alloc((size_t)s.br_elems() * c);
-  int batch = 2 * s.nk;
-  w.proj.alloc((size_t)batch * s.nproj * 2 * s.nb * c + c);
-  w.dmix.alloc((size_t)batch * s.nproj * 2 * s.nb * c + c);
-  w.ovl.alloc((size_t)batch * s.nb * s.nb * c);
+  if (w.ready && w.nvec_cap >= nvec) return;
+  const size_t c = sizeof(cx<T>), nv = (size_t)nvec;
+  w.ready = false;
+  w.xr.alloc(nv * s.rows() * s.nr * c);
+  w.rho.alloc(nv * 4 * (size_t)s.nr * c);
+  w.rhopart.alloc((size_t)kDensityGroups * nv * 4 * (size_t)s.nr * c);
+  w.vpot.alloc(nv * 4 * (size_t)s.nr * c);
+  w.hgrid.alloc(nv * (size_t)s.nr * c);
+  w.h.alloc(nv * (size_t)s.br_elems() * c);
+  w.xin.alloc(nv * (size_t)s.br_elems() * c);
+  size_t batch = nv * 2 * s.nk;
+  w.proj.alloc(batch * s.nproj * 2 * s.nb * c + c);
+  w.dmix.alloc(batch * s.nproj * 2 * s.nb * c + c);
+  w.ovl.alloc(batch * s.nb * s.nb * c);
   size_t p1 = (size_t)32 * batch * std::max(s.nproj, 1) * 2 * s.nb;
   size_t p2 = (size_t)32 * batch * s.nb * s.nb;
   w.part.alloc(std::max(p1, p2) * c);
+  w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
+  w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+  w.nvec_cap = nvec;
   w.ready = true;
+}
+
+// a[i] *= fac[i % n] (the Hartree factor of one grid applied to stacked grids)
+template <class T>
+__global__ void scale_periodic_kernel(cx<T> *__restrict__ a, const T *__restrict__ fac,
+                                      long long n, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    a[i] = cscale<T>(a[i], fac[i % n]);
+}
+
+// b[v][i] = a[v][stride][i]  (component 0 of each vector's 4-component density)
+template <class T>
+__global__ void gather_component_kernel(const cx<T> *__restrict__ a, cx<T> *__restrict__ b,
+                                        long long n, long long stride, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long v = i / n;
+    b[i] = a[v * stride + (i - v * n)];
+  }
 }
 
 }  // namespace
@@ -634,6 +691,7 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     TDLZ_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
   };
   s.plan.init(gs->fft);
+  build_stick_tables(s, idx_kq);
   up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
   up(s.idx_kq, idx_kq.data(), idx_kq.size() * sizeof(int));
   up(s.map_kq_k, map.data(), map.size() * sizeof(int));
@@ -702,100 +760,96 @@ void ensure_precision(Context &ctx, QSlot &s) {
       f.ready = true;
     }
   }
-  alloc_workspace<T>(s);
+  alloc_workspace<T>(s, std::max(1, slot_ws<T>(s).nvec_cap));
 }
 
 // ==================================================================== apply
 template <class T>
-void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool adjoint) {
+void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nvec,
+                       unsigned adj_mask) {
+  TDLZ_REQUIRE(nvec >= 1 && nvec <= 32, TDLZ_ERR_ARG, "nvec must be in [1, 32]");
   ensure_precision<T>(ctx, s);
+  alloc_workspace<T>(s, nvec);
   SlotData<T> &d = slot_data<T>(s);
   Workspace<T> &w = slot_ws<T>(s);
   cudaStream_t st = ctx.stream;
   Profiler &pf = ctx.prof;
   const int nk = s.nk, nb = s.nb, npwx = s.npwx, np_ = s.nproj;
-  const long long nr = s.nr, rows = s.rows(), nbs = rows / 2;
-  const int batch = 2 * nk;
+  const long long nr = s.nr, rows = s.rows() * nvec, nbs = rows / 2, br = s.br_elems();
+  const int batch1 = 2 * nk, batch = batch1 * nvec;
   // algorithmic traffic / work per stage (see the design doc for the definitions)
   const double c = sizeof(cx<T>), re = sizeof(T);
-  const double V = (double)s.br_elems(), G = (double)rows * nr;
+  const double V = (double)br * nvec, G = (double)rows * nr, Gu = (double)s.rows() * nr;
   const double fft_flops = (double)rows * 5.0 * nr * std::log2((double)nr);
-  if (adjoint) {  // L^H x = J L J x
+  if (adj_mask) {  // L^H x = J L J x for the flagged vectors
     ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
-    jflip_copy<T>(ctx, s, x, w.xin.template as<cx<T>>());
-    x = w.xin.template as<cx<T>>();
+    cx<T> *xin = w.xin.template as<cx<T>>();
+    for (int v = 0; v < nvec; ++v) {
+      if (adj_mask >> v & 1u)
+        jflip_copy<T>(ctx, s, x + v * br, xin + v * br);
+      else
+        TDLZ_CUDA_TRY(cudaMemcpyAsync(xin + v * br, x + v * br, br * sizeof(cx<T>),
+                                      cudaMemcpyDeviceToDevice, st));
+    }
+    x = xin;
   }
   cx<T> *xr = w.xr.template as<cx<T>>();
-  // 1. sphere -> grid -> real space
+  cx<T> *i1 = w.i1.template as<cx<T>>(), *i2 = w.i2.template as<cx<T>>();
+  // pruned traffic: stick buffer (rows x nstick x n3) and plane buffer (rows x nplane x n2 x n3)
+  const double S1 = (double)rows * s.nstick_max * s.fft[2];
+  const double S2 = (double)rows * s.nplane_max * s.fft[1] * s.fft[2];
+  // 1. sphere -> real space (pruned Z, Y passes; full X pass)
   {
-    ProfScope ps(pf, st, ST_SCATTER, V * c + G * c, 0);
-    TDLZ_CUDA_TRY(cudaMemsetAsync(xr, 0, w.xr.bytes, st));
-    scatter_rows_kernel<T><<<row_grid(rows, npwx), kThreads, 0, st>>>(
-        x, xr, s.idx_kq.as<int>(), nk, nb, npwx, nr, (T)(1.0 / std::sqrt(s.omega)), rows);
-    TDLZ_LAUNCH_CHECK();
+    ProfScope ps(pf, st, ST_FFT_INV, V * c + 2 * S1 * c + 2 * S2 * c + G * c, fft_flops);
+    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);
   }
-  {
-    ProfScope ps(pf, st, ST_FFT_INV, 3 * 2 * G * c, fft_flops);
-    fft3d<T>(s.plan, xr, rows, +1, st);
-  }
-  // 2-4. densities and HXC potential
+  // 2-4. densities and HXC potentials (one set per vector)
   cx<T> *rho = w.rho.template as<cx<T>>();
   cx<T> *vp = w.vpot.template as<cx<T>>();
   cx<T> *hg = w.hgrid.template as<cx<T>>();
   const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
   if (use_h || use_xc) {
     {
-      ProfScope ps(pf, st, ST_DENSITY, 2 * G * c + 4 * nr * c, (double)nbs * nr * 40.0);
-      density_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(d.ur.template as<cx<T>>(), xr,
-                                                            d.wk.template as<T>(), rho, nk, nb, nr);
-      TDLZ_LAUNCH_CHECK();
+      ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
+                   (double)nbs * nr * 40.0);
+      launch_density<T>(st, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
+                        w.rhopart.template as<cx<T>>(), nk, nb, nr, nvec);
     }
     if (use_h) {
-      ProfScope ps(pf, st, ST_HARTREE, 8 * nr * c, 2 * 5.0 * nr * std::log2((double)nr));
-      copy_scale_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(rho, hg, nullptr, nr);
+      ProfScope ps(pf, st, ST_HARTREE, 8.0 * nvec * nr * c,
+                   2 * 5.0 * nvec * nr * std::log2((double)nr));
+      long long tot = (long long)nvec * nr;
+      gather_component_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(rho, hg, nr, 4 * nr, tot);
       TDLZ_LAUNCH_CHECK();
-      fft3d<T>(s.plan, hg, 1, -1, st);
-      scale_inplace_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(hg, d.vhfac.template as<T>(),
-                                                                  nr);
+      fft3d<T>(s.plan, hg, nvec, -1, st);
+      scale_periodic_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
+          hg, d.vhfac.template as<T>(), nr, tot);
       TDLZ_LAUNCH_CHECK();
-      fft3d<T>(s.plan, hg, 1, +1, st);
+      fft3d<T>(s.plan, hg, nvec, +1, st);
     }
-    ProfScope ps(pf, st, ST_POTENTIAL, 9 * nr * c + 10 * nr * re, 16.0 * 4 * nr);
-    potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(rho, hg, d.fxc.template as<T>(), vp,
-                                                            nr, use_h ? 1 : 0, use_xc ? 1 : 0);
-    TDLZ_LAUNCH_CHECK();
+    ProfScope ps(pf, st, ST_POTENTIAL, nvec * (9 * nr * c + 10 * nr * re),
+                 16.0 * 4 * nr * nvec);
+    for (int v = 0; v < nvec; ++v) {
+      potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(
+          rho + (long long)v * 4 * nr, hg + (long long)v * nr, d.fxc.template as<T>(),
+          vp + (long long)v * 4 * nr, nr, use_h ? 1 : 0, use_xc ? 1 : 0);
+      TDLZ_LAUNCH_CHECK();
+    }
   } else {
     TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
   }
-  // 5. local products in place
-  {
-    ProfScope ps(pf, st, ST_PRODUCT, 3 * G * c + 4 * nr * (c + re), (double)nbs * nr * 64.0);
-    unsigned bx = blocks_for(nr);
-    if (bx > 64) bx = 64;
-    long long yz = nbs, z = 1;
-    while (yz > 65535) {
-      z *= 2;
-      yz = (nbs + z - 1) / z;
-    }
-    product_kernel<T><<<dim3(bx, (unsigned)yz, (unsigned)z), kThreads, 0, st>>>(
-        xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(), d.bfield.template as<T>(), vp, nk,
-        nb, nr, nbs);
-    TDLZ_LAUNCH_CHECK();
-  }
-  // 6. real space -> sphere, + (kin - e) x
-  {
-    ProfScope ps(pf, st, ST_FFT_FWD, 3 * 2 * G * c, fft_flops);
-    fft3d<T>(s.plan, xr, rows, -1, st);
-  }
+  // 5-6. local products fused into the forward X pass; pruned Y, Z passes with the
+  //      sphere gather and + (kin - e) x fused into the last one
   cx<T> *h = w.h.template as<cx<T>>();
   {
-    ProfScope ps(pf, st, ST_GATHER, 3 * V * c + V / 2 * re, 6.0 * V);
-    gather_rows_kernel<T><<<row_grid(rows, npwx), kThreads, 0, st>>>(
-        xr, x, h, s.idx_kq.as<int>(), d.kin.template as<T>(), d.evals.template as<T>(), nk, nb,
-        npwx, nr, (T)(std::sqrt(s.omega) / nr), rows);
-    TDLZ_LAUNCH_CHECK();
+    ProfScope ps(pf, st, ST_FFT_FWD,
+                 G * c + Gu * c + 4 * nvec * nr * (c + re) + 2 * S2 * c + 2 * S1 * c + 3 * V * c,
+                 fft_flops + (double)nbs * nr * 64.0);
+    pipeline_forward<T>(ctx, s, x, xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(),
+                        d.bfield.template as<T>(), vp, d.kin.template as<T>(),
+                        d.evals.template as<T>(), i1, i2, h, nvec);
   }
-  // 7. nonlocal pseudopotential
+  // 7. nonlocal pseudopotential (projector tables shared by all vectors: batch b -> k = b % nk)
   const long long bstride = (long long)nb * 2 * npwx;
   if (np_ > 0) {
     double bb = (double)nk * np_ * npwx * c;
@@ -813,19 +867,22 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, bool ad
                (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
                batch);
   }
-  // 8. P_c and the row sign
+  // 8. P_c and the row sign (occupied k+q states shared: batch b -> (side, k) = b % 2nk;
+  //    Y-side batches (b % 2nk >= nk) negated)
   {
-    ProfScope ps(pf, st, ST_PC, 5 * V * c, 2 * 8.0 * batch * (double)nb * nb * 2 * npwx);
+    ProfScope ps(pf, st, ST_PC, 4 * V * c + (double)br * c,
+                 2 * 8.0 * batch * (double)nb * nb * 2 * npwx);
     cx<T> *ov = w.ovl.template as<cx<T>>();
     const cx<T> *ukq = d.ukq.template as<cx<T>>();
-    gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch, h, 2LL * npwx, bstride, ov,
+    gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch1, h, 2LL * npwx, bstride, ov,
                (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
-    gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch, h, y,
-               2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk);
+    gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h, y,
+               2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk, batch1);
   }
-  if (adjoint) {
+  if (adj_mask) {
     ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
-    jflip_copy<T>(ctx, s, y, y);
+    for (int v = 0; v < nvec; ++v)
+      if (adj_mask >> v & 1u) jflip_copy<T>(ctx, s, y + v * br, y + v * br);
   }
 }
 
@@ -864,8 +921,10 @@ void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v) {
 
 template void ensure_precision<double>(Context &, QSlot &);
 template void ensure_precision<float>(Context &, QSlot &);
-template void apply_liouvillian<double>(Context &, QSlot &, const double2 *, double2 *, bool);
-template void apply_liouvillian<float>(Context &, QSlot &, const float2 *, float2 *, bool);
+template void apply_liouvillian<double>(Context &, QSlot &, const double2 *, double2 *, int,
+                                        unsigned);
+template void apply_liouvillian<float>(Context &, QSlot &, const float2 *, float2 *, int,
+                                       unsigned);
 template void start_vector<double>(Context &, QSlot &, int, double2 *);
 template void start_vector<float>(Context &, QSlot &, int, float2 *);
 

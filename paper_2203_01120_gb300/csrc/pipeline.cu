@@ -1,0 +1,786 @@
+// Pruned, fused plane-wave <-> real-space transforms of the Liouvillian.
+//
+// A k+q sphere touches only a fraction of the FFT box: its (m1, m2) "sticks"
+// (~20% of the z-lines at C2) and its m1 "planes" (~50% of the x-planes).  The
+// inverse transform therefore runs
+//   Z: sticks only, reading the sphere coefficients directly (no zeroed grid, no
+//      separate scatter),
+//   Y: only the planes that hold sticks, lines assembled from the stick buffer,
+//   X: every column, lines assembled from the plane buffer -> x(r),
+// and the forward transform mirrors it:
+//   X: every column, with [v_loc + s B.sigma] x + W^s U formed while loading
+//      (the product stage is fused), keeping only the sphere's planes,
+//   Y: keeping only the sphere's sticks,
+//   Z: writing only sphere coefficients, fused with + (|k+q+G|^2/2 - e_n) x.
+// Each pass runs the Stockham line transform of fft.cu's axis kernel on a tile
+// of TL lines held in shared memory as [position][TL + 1].
+#include <cmath>
+
+#include "pipeline.cuh"
+#include "regfft.cuh"
+
+// Launch KERNEL<T, N>(args) for the register-line lengths; sets ok = false otherwise.
+#define TDLZ_REG_LAUNCH(n, KERNEL, grid, ...)                                          \
+  switch (n) {                                                                       \
+    case 12: KERNEL<T, 12><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 16: KERNEL<T, 16><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 24: KERNEL<T, 24><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 36: KERNEL<T, 36><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 45: KERNEL<T, 45><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 48: KERNEL<T, 48><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    default: ok = false;                                                             \
+  }
+
+namespace tdlz {
+
+namespace {
+
+struct St {
+  int nrad;
+  int radix[8];
+};
+
+St stages(const AxisPlan &a) {
+  St s;
+  s.nrad = a.nrad;
+  for (int i = 0; i < 8; ++i) s.radix[i] = a.radix[i];
+  return s;
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> twr(const cx<T> *tw, int t, int dir) {
+  cx<T> w = tw[t];
+  if (dir < 0) w.y = -w.y;
+  return w;
+}
+
+// Stockham transform of TL lines of length n held at in[j * P + l]; returns the
+// buffer (in or out) that holds the result.  Called by all threads of the block.
+template <class T, int TL>
+__device__ cx<T> *tile_fft(cx<T> *in, cx<T> *out, int n, const St &st, const cx<T> *tw,
+                           int dir) {
+  constexpr int P = TL + 1;
+  cx<T> w3 = czero<T>(), w5a = czero<T>(), w5b = czero<T>();
+  if (n % 3 == 0) w3 = twr<T>(tw, n / 3, dir);
+  if (n % 5 == 0) {
+    w5a = twr<T>(tw, n / 5, dir);
+    w5b = twr<T>(tw, (2 * n) / 5, dir);
+  }
+  int ns = 1;
+  for (int s = 0; s < st.nrad; ++s) {
+    const int R = st.radix[s];
+    const int nR = n / R;
+    const int tstride = n / (ns * R);
+    for (int b = threadIdx.x; b < nR * TL; b += blockDim.x) {
+      const int j = b / TL;
+      const int l = b - j * TL;
+      const int k = j % ns;
+      cx<T> v[5];
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (r < R) v[r] = in[(j + r * nR) * P + l];
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < 5; ++r)
+          if (r < R) v[r] = cmul<T>(v[r], twr<T>(tw, (r * k * tstride) % n, dir));
+      }
+      if (R == 2) {
+        cx<T> a = v[0];
+        v[0] = cadd<T>(a, v[1]);
+        v[1] = csub<T>(a, v[1]);
+      } else if (R == 4) {
+        cx<T> a = cadd<T>(v[0], v[2]), bb = csub<T>(v[0], v[2]);
+        cx<T> c = cadd<T>(v[1], v[3]), d = csub<T>(v[1], v[3]);
+        cx<T> e = dir > 0 ? mk<T>(-d.y, d.x) : mk<T>(d.y, -d.x);
+        v[0] = cadd<T>(a, c);
+        v[2] = csub<T>(a, c);
+        v[1] = cadd<T>(bb, e);
+        v[3] = csub<T>(bb, e);
+      } else if (R == 3) {
+        cx<T> sm = cadd<T>(v[1], v[2]), df = csub<T>(v[1], v[2]);
+        cx<T> m = mk<T>(v[0].x + w3.x * sm.x, v[0].y + w3.x * sm.y);
+        cx<T> rr = mk<T>(-w3.y * df.y, w3.y * df.x);
+        v[0] = cadd<T>(v[0], sm);
+        v[1] = cadd<T>(m, rr);
+        v[2] = csub<T>(m, rr);
+      } else {
+        cx<T> a1 = cadd<T>(v[1], v[4]), b1 = csub<T>(v[1], v[4]);
+        cx<T> a2 = cadd<T>(v[2], v[3]), b2 = csub<T>(v[2], v[3]);
+        T c1 = w5a.x, s1 = w5a.y, c2 = w5b.x, s2 = w5b.y;
+        cx<T> m1 = mk<T>(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+        cx<T> m2 = mk<T>(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+        cx<T> p1 = mk<T>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
+        cx<T> p2 = mk<T>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
+        v[0] = cadd<T>(v[0], cadd<T>(a1, a2));
+        v[1] = cadd<T>(m1, p1);
+        v[4] = csub<T>(m1, p1);
+        v[2] = cadd<T>(m2, p2);
+        v[3] = csub<T>(m2, p2);
+      }
+      const int ob = (j / ns) * ns * R + k;
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (r < R) out[(ob + r * ns) * P + l] = v[r];
+    }
+    __syncthreads();
+    cx<T> *t = in;
+    in = out;
+    out = t;
+    ns *= R;
+  }
+  return in;
+}
+
+__device__ __forceinline__ long long row_of_block() {
+  return blockIdx.y + (long long)gridDim.y * blockIdx.z;
+}
+
+// ---------------------------------------------------------------- inverse
+// Z pass: sticks of row `row`, tile of TL sticks; sphere coefficients gathered.
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    inv_z_kernel(const cx<T> *__restrict__ x, cx<T> *__restrict__ i1, const int *__restrict__ nst,
+                 const int *__restrict__ smap, int nk, int nb, int npwx, int nsm, int n3, T scale,
+                 long long rows, St st, const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long row = row_of_block();
+  if (row >= rows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  int s0 = blockIdx.x * TL;
+  int nl = min(TL, nst[k] - s0);
+  if (nl <= 0) return;
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n3 * P;
+  const int *mp = smap + ((long long)k * nsm + s0) * n3;
+  const cx<T> *xr = x + row * npwx;
+  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+    int l = e / n3, j = e - l * n3;
+    cx<T> v = czero<T>();
+    if (l < nl) {
+      int g = mp[l * n3 + j];
+      if (g >= 0) v = cscale<T>(xr[g], scale);
+    }
+    b0[j * P + l] = v;
+  }
+  __syncthreads();
+  cx<T> *res = tile_fft<T, TL>(b0, b1, n3, st, tw, +1);
+  cx<T> *o = i1 + (row * nsm + s0) * n3;
+  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+    int l = e / n3, j = e - l * n3;
+    if (l < nl) o[(long long)l * n3 + j] = res[j * P + l];
+  }
+}
+
+// Y pass: plane p of row, tile of TL consecutive j3; lines assembled from sticks.
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    inv_y_kernel(const cx<T> *__restrict__ i1, cx<T> *__restrict__ i2, const int *__restrict__ npl,
+                 const int *__restrict__ sid, int nk, int nb, int nsm, int npm, int n2, int n3,
+                 long long rows, St st, const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long rp = row_of_block();  // (row, plane) flattened
+  if (rp >= rows * npm) return;
+  long long row = rp / npm;
+  int p = (int)(rp - row * npm);
+  int k = (int)((row / (2 * nb)) % nk);
+  if (p >= npl[k]) return;
+  int j0 = blockIdx.x * TL;
+  int nl = min(TL, n3 - j0);
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n2 * P;
+  const int *sd = sid + ((long long)k * npm + p) * n2;
+  const cx<T> *src = i1 + row * nsm * (long long)n3;
+  for (int e = threadIdx.x; e < n2 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    cx<T> v = czero<T>();
+    int s = sd[j];
+    if (s >= 0 && l < nl) v = src[(long long)s * n3 + j0 + l];
+    b0[j * P + l] = v;
+  }
+  __syncthreads();
+  cx<T> *res = tile_fft<T, TL>(b0, b1, n2, st, tw, +1);
+  cx<T> *o = i2 + ((row * npm + p) * n2) * (long long)n3 + j0;
+  for (int e = threadIdx.x; e < n2 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    if (l < nl) o[(long long)j * n3 + l] = res[j * P + l];
+  }
+}
+
+// X pass: every (j2, j3) column tile; lines assembled from planes -> x(r).
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    inv_x_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ xr, const int *__restrict__ plof,
+                 int nk, int nb, int npm, int n1, long long n23, long long nr, long long rows, St st,
+                 const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long row = row_of_block();
+  if (row >= rows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  long long c0 = (long long)blockIdx.x * TL;
+  int nl = (int)min((long long)TL, n23 - c0);
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n1 * P;
+  const int *po = plof + (long long)k * n1;
+  const cx<T> *src = i2 + row * npm * n23 + c0;
+  for (int e = threadIdx.x; e < n1 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    cx<T> v = czero<T>();
+    int p = po[j];
+    if (p >= 0 && l < nl) v = src[(long long)p * n23 + l];
+    b0[j * P + l] = v;
+  }
+  __syncthreads();
+  cx<T> *res = tile_fft<T, TL>(b0, b1, n1, st, tw, +1);
+  cx<T> *o = xr + row * nr + c0;
+  for (int e = threadIdx.x; e < n1 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    if (l < nl) o[(long long)j * n23 + l] = res[j * P + l];
+  }
+}
+
+// ---------------------------------------------------------------- forward
+// X pass with the local products: band-side bs (both spinor rows), column tile.
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    fwd_x_product_kernel(const cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
+                         const T *__restrict__ vloc, const T *__restrict__ bf,
+                         const cx<T> *__restrict__ v, cx<T> *__restrict__ i2,
+                         const int *__restrict__ npl, const int *__restrict__ plj, int nk, int nb,
+                         int npm, int n1, long long n23, long long nr, long long nbs, St st,
+                         const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long bs = row_of_block();  // band-side over all stacked vectors
+  if (bs >= nbs) return;
+  const long long nbs1 = 2LL * nk * nb;  // band-sides per vector
+  const long long vec = bs / nbs1, bs1 = bs - vec * nbs1;
+  int k = (int)((bs1 / nb) % nk);
+  int side = (int)(bs1 / ((long long)nk * nb));
+  T s = side == 0 ? T(1) : T(-1);
+  v += vec * 4 * nr;     // this vector's HXC potential
+  ur += 2 * bs1 * nr;    // its occupied orbitals (shared by all vectors)
+  long long c0 = (long long)blockIdx.x * TL;
+  int nl = (int)min((long long)TL, n23 - c0);
+  cx<T> *a0 = reinterpret_cast<cx<T> *>(smem_raw), *a1 = a0 + n1 * P;
+  cx<T> *q0 = a1 + n1 * P, *q1 = q0 + n1 * P;
+  long long r0 = 2 * bs;
+  for (int e = threadIdx.x; e < n1 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    cx<T> t0 = czero<T>(), t1 = czero<T>();
+    if (l < nl) {
+      long long r = (long long)j * n23 + c0 + l;
+      T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
+      cx<T> v0 = v[r], v1 = v[nr + r], v2 = v[2 * nr + r], v3 = v[3 * nr + r];
+      cx<T> x0 = xr[r0 * nr + r], x1 = xr[(r0 + 1) * nr + r];
+      cx<T> u0 = ur[r], u1 = ur[nr + r];
+      cx<T> h01 = mk<T>(s * bx, -s * by), h10 = mk<T>(s * bx, s * by);
+      t0 = cscale<T>(x0, vl + s * bz);
+      cfma<T>(t0, h01, x1);
+      t1 = cscale<T>(x1, vl - s * bz);
+      cfma<T>(t1, h10, x0);
+      cx<T> w00 = mk<T>(v0.x + s * v3.x, v0.y + s * v3.y);
+      cx<T> w11 = mk<T>(v0.x - s * v3.x, v0.y - s * v3.y);
+      cx<T> w01 = mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x));
+      cx<T> w10 = mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x));
+      cfma<T>(t0, w00, u0);
+      cfma<T>(t0, w01, u1);
+      cfma<T>(t1, w10, u0);
+      cfma<T>(t1, w11, u1);
+    }
+    a0[j * P + l] = t0;
+    q0[j * P + l] = t1;
+  }
+  __syncthreads();
+  cx<T> *ra = tile_fft<T, TL>(a0, a1, n1, st, tw, -1);
+  cx<T> *rb = tile_fft<T, TL>(q0, q1, n1, st, tw, -1);
+  int np_ = npl[k];
+  const int *pj = plj + (long long)k * npm;
+  for (int e = threadIdx.x; e < np_ * TL; e += blockDim.x) {
+    int p = e / TL, l = e - p * TL;
+    if (l >= nl) continue;
+    int j = pj[p];
+    i2[((r0 * npm) + p) * n23 + c0 + l] = ra[j * P + l];
+    i2[(((r0 + 1) * npm) + p) * n23 + c0 + l] = rb[j * P + l];
+  }
+}
+
+// Y pass: plane p, tile of TL j3; keeps only the sphere's sticks.
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    fwd_y_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ i1, const int *__restrict__ npl,
+                 const int *__restrict__ sid, int nk, int nb, int nsm, int npm, int n2, int n3,
+                 long long rows, St st, const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long rp = row_of_block();  // (row, plane) flattened
+  if (rp >= rows * npm) return;
+  long long row = rp / npm;
+  int p = (int)(rp - row * npm);
+  int k = (int)((row / (2 * nb)) % nk);
+  if (p >= npl[k]) return;
+  int j0 = blockIdx.x * TL;
+  int nl = min(TL, n3 - j0);
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n2 * P;
+  const cx<T> *src = i2 + ((row * npm + p) * n2) * (long long)n3 + j0;
+  for (int e = threadIdx.x; e < n2 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    b0[j * P + l] = l < nl ? src[(long long)j * n3 + l] : czero<T>();
+  }
+  __syncthreads();
+  cx<T> *res = tile_fft<T, TL>(b0, b1, n2, st, tw, -1);
+  const int *sd = sid + ((long long)k * npm + p) * n2;
+  cx<T> *o = i1 + row * nsm * (long long)n3 + j0;
+  for (int e = threadIdx.x; e < n2 * TL; e += blockDim.x) {
+    int j = e / TL, l = e - j * TL;
+    int s = sd[j];
+    if (s >= 0 && l < nl) o[(long long)s * n3 + l] = res[j * P + l];
+  }
+}
+
+// Z pass: sticks; writes sphere coefficients + (kin - e) x.
+template <class T, int TL>
+__global__ void __launch_bounds__(256)
+    fwd_z_gather_kernel(const cx<T> *__restrict__ i1, const cx<T> *__restrict__ x,
+                        cx<T> *__restrict__ h, const int *__restrict__ nst,
+                        const int *__restrict__ smap, const T *__restrict__ kin,
+                        const T *__restrict__ evals, int nk, int nb, int npwx, int nsm, int n3,
+                        T scale, long long rows, St st, const cx<T> *__restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int P = TL + 1;
+  long long row = row_of_block();
+  if (row >= rows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  int s0 = blockIdx.x * TL;
+  int nl = min(TL, nst[k] - s0);
+  if (nl <= 0) return;
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n3 * P;
+  const cx<T> *src = i1 + (row * nsm + s0) * n3;
+  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+    int l = e / n3, j = e - l * n3;
+    b0[j * P + l] = l < nl ? src[(long long)l * n3 + j] : czero<T>();
+  }
+  __syncthreads();
+  cx<T> *res = tile_fft<T, TL>(b0, b1, n3, st, tw, -1);
+  const int *mp = smap + ((long long)k * nsm + s0) * n3;
+  T e_n = evals[(row / 2) % (2LL * nk * nb)];
+  const T *kk = kin + (long long)k * npwx;
+  const cx<T> *xrow = x + row * npwx;
+  cx<T> *hrow = h + row * npwx;
+  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+    int l = e / n3, j = e - l * n3;
+    if (l >= nl) continue;
+    int g = mp[l * n3 + j];
+    if (g < 0) continue;
+    cx<T> r = res[j * P + l];
+    cx<T> xv = xrow[g];
+    T d = kk[g] - e_n;
+    hrow[g] = mk<T>(r.x * scale + d * xv.x, r.y * scale + d * xv.y);
+  }
+}
+
+// ------------------------------------------- register-line variants (x, y axes)
+// One thread per line, the whole line in registers (regfft.cuh); neighbouring
+// threads own neighbouring lines, so each load/store of a warp is coalesced.
+constexpr int kRegThreads = 128;
+
+template <class T, int N1>
+__global__ void __launch_bounds__(kRegThreads)
+    inv_x_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ xr,
+                     const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
+                     long long nr, long long rows, const cx<T> *__restrict__ tw) {
+  long long row = row_of_block();
+  if (row >= rows) return;
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n23) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  const int *po = plof + (long long)k * N1;
+  const cx<T> *src = i2 + row * npm * n23 + c;
+  cx<T> a[N1];
+#pragma unroll
+  for (int j = 0; j < N1; ++j) {
+    int p = __ldg(po + j);
+    a[j] = p >= 0 ? src[(long long)p * n23] : czero<T>();
+  }
+  RegPlan<N1>::template run<T, +1>(a, tw);
+  cx<T> *o = xr + row * nr + c;
+#pragma unroll
+  for (int j = 0; j < N1; ++j) o[(long long)j * n23] = a[j];
+}
+
+template <class T, int N2>
+__global__ void __launch_bounds__(kRegThreads)
+    inv_y_reg_kernel(const cx<T> *__restrict__ i1, cx<T> *__restrict__ i2,
+                     const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
+                     int nsm, int npm, int n3, long long rows, const cx<T> *__restrict__ tw) {
+  long long row = row_of_block();
+  if (row >= rows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (plane, j3)
+  int p = (int)(idx / n3), j3 = (int)(idx - (long long)p * n3);
+  if (p >= __ldg(npl + k)) return;
+  const int *sd = sid + ((long long)k * npm + p) * N2;
+  const cx<T> *src = i1 + row * nsm * (long long)n3 + j3;
+  cx<T> a[N2];
+#pragma unroll
+  for (int j = 0; j < N2; ++j) {
+    int s = __ldg(sd + j);
+    a[j] = s >= 0 ? src[(long long)s * n3] : czero<T>();
+  }
+  RegPlan<N2>::template run<T, +1>(a, tw);
+  cx<T> *o = i2 + ((row * npm + p) * N2) * (long long)n3 + j3;
+#pragma unroll
+  for (int j = 0; j < N2; ++j) o[(long long)j * n3] = a[j];
+}
+
+// Forward X pass with the products: thread per (band-side, column, spinor).
+template <class T, int N1>
+__global__ void __launch_bounds__(kRegThreads)
+    fwd_x_product_reg_kernel(const cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
+                             const T *__restrict__ vloc, const T *__restrict__ bf,
+                             const cx<T> *__restrict__ v, cx<T> *__restrict__ i2,
+                             const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
+                             long long nr, long long nbs, int nvec,
+                             const cx<T> *__restrict__ tw) {
+  long long blk = row_of_block();
+  if (blk >= nbs) return;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long c = t >> 1;
+  const int sp = (int)(t & 1);
+  if (c >= n23) return;
+  // the vectors of one band-side are adjacent in the launch order, so the occupied
+  // orbitals they share are re-read from L2 rather than HBM
+  const long long nbs1 = 2LL * nk * nb;
+  const long long bs1 = blk / nvec, vec = blk - bs1 * nvec;
+  const long long bs = vec * nbs1 + bs1;
+  const int k = (int)((bs1 / nb) % nk);
+  const T s = (bs1 / ((long long)nk * nb)) == 0 ? T(1) : T(-1);
+  v += vec * 4 * nr;
+  ur += 2 * bs1 * nr;
+  const long long r0 = 2 * bs;
+  const cx<T> *x0p = xr + r0 * nr, *x1p = xr + (r0 + 1) * nr;
+  cx<T> a[N1];
+#pragma unroll
+  for (int j = 0; j < N1; ++j) {
+    long long r = (long long)j * n23 + c;
+    T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
+    cx<T> v0 = v[r], v1 = v[nr + r], v2 = v[2 * nr + r], v3 = v[3 * nr + r];
+    cx<T> x0 = x0p[r], x1 = x1p[r], u0 = ur[r], u1 = ur[nr + r];
+    cx<T> res;
+    if (sp == 0) {  // [vl + s bz] x0 + s(bx - i by) x1 + (v0 + s v3) u0 + s(v1 - i v2) u1
+      res = cscale<T>(x0, vl + s * bz);
+      cfma<T>(res, mk<T>(s * bx, -s * by), x1);
+      cfma<T>(res, mk<T>(v0.x + s * v3.x, v0.y + s * v3.y), u0);
+      cfma<T>(res, mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x)), u1);
+    } else {  // s(bx + i by) x0 + [vl - s bz] x1 + s(v1 + i v2) u0 + (v0 - s v3) u1
+      res = cscale<T>(x1, vl - s * bz);
+      cfma<T>(res, mk<T>(s * bx, s * by), x0);
+      cfma<T>(res, mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x)), u0);
+      cfma<T>(res, mk<T>(v0.x - s * v3.x, v0.y - s * v3.y), u1);
+    }
+    a[j] = res;
+  }
+  RegPlan<N1>::template run<T, -1>(a, tw);
+  const int *po = plof + (long long)k * N1;
+  cx<T> *o = i2 + (r0 + sp) * npm * n23 + c;
+#pragma unroll
+  for (int j = 0; j < N1; ++j) {
+    int p = __ldg(po + j);
+    if (p >= 0) o[(long long)p * n23] = a[j];
+  }
+}
+
+// Local products, elementwise and in place over x(r): one thread per (band-side,
+// point) handles that band-side for every stacked vector, so U(r) is read once.
+//   t0 = [vl + s bz] x0 + s(bx - i by) x1 + (v0 + s v3) u0 + s(v1 - i v2) u1
+//   t1 = s(bx + i by) x0 + [vl - s bz] x1 + s(v1 + i v2) u0 + (v0 - s v3) u1
+template <class T>
+__global__ void __launch_bounds__(256)
+    product_group_kernel(cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
+                         const T *__restrict__ vloc, const T *__restrict__ bf,
+                         const cx<T> *__restrict__ v, int nk, int nb, long long nr, int nvec) {
+  const long long bs1 = row_of_block();  // band-side of one vector
+  const long long nbs1 = 2LL * nk * nb;
+  if (bs1 >= nbs1) return;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const T s = (bs1 / ((long long)nk * nb)) == 0 ? T(1) : T(-1);
+  const cx<T> u0 = ur[2 * bs1 * nr + r], u1 = ur[(2 * bs1 + 1) * nr + r];
+  const T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
+  const cx<T> h01 = mk<T>(s * bx, -s * by), h10 = mk<T>(s * bx, s * by);
+  for (int vec = 0; vec < nvec; ++vec) {
+    const cx<T> *vv = v + (long long)vec * 4 * nr;
+    const cx<T> v0 = vv[r], v1 = vv[nr + r], v2 = vv[2 * nr + r], v3 = vv[3 * nr + r];
+    const long long r0 = 2 * (vec * nbs1 + bs1);
+    cx<T> x0 = xr[r0 * nr + r], x1 = xr[(r0 + 1) * nr + r];
+    cx<T> t0 = cscale<T>(x0, vl + s * bz);
+    cfma<T>(t0, h01, x1);
+    cfma<T>(t0, mk<T>(v0.x + s * v3.x, v0.y + s * v3.y), u0);
+    cfma<T>(t0, mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x)), u1);
+    cx<T> t1 = cscale<T>(x1, vl - s * bz);
+    cfma<T>(t1, h10, x0);
+    cfma<T>(t1, mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x)), u0);
+    cfma<T>(t1, mk<T>(v0.x - s * v3.x, v0.y - s * v3.y), u1);
+    xr[r0 * nr + r] = t0;
+    xr[(r0 + 1) * nr + r] = t1;
+  }
+}
+
+// Forward X pass in registers over the products; keeps only the sphere's planes.
+template <class T, int N1>
+__global__ void __launch_bounds__(kRegThreads)
+    fwd_x_reg_kernel(const cx<T> *__restrict__ xr, cx<T> *__restrict__ i2,
+                     const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
+                     long long nr, long long rows, const cx<T> *__restrict__ tw) {
+  long long row = row_of_block();
+  if (row >= rows) return;
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n23) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  const cx<T> *src = xr + row * nr + c;
+  cx<T> a[N1];
+#pragma unroll
+  for (int j = 0; j < N1; ++j) a[j] = src[(long long)j * n23];
+  RegPlan<N1>::template run<T, -1>(a, tw);
+  const int *po = plof + (long long)k * N1;
+  cx<T> *o = i2 + row * npm * n23 + c;
+#pragma unroll
+  for (int j = 0; j < N1; ++j) {
+    int p = __ldg(po + j);
+    if (p >= 0) o[(long long)p * n23] = a[j];
+  }
+}
+
+template <class T, int N2>
+__global__ void __launch_bounds__(kRegThreads)
+    fwd_y_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ i1,
+                     const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
+                     int nsm, int npm, int n3, long long rows, const cx<T> *__restrict__ tw) {
+  long long row = row_of_block();
+  if (row >= rows) return;
+  int k = (int)((row / (2 * nb)) % nk);
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int p = (int)(idx / n3), j3 = (int)(idx - (long long)p * n3);
+  if (p >= __ldg(npl + k)) return;
+  const cx<T> *src = i2 + ((row * npm + p) * N2) * (long long)n3 + j3;
+  cx<T> a[N2];
+#pragma unroll
+  for (int j = 0; j < N2; ++j) a[j] = src[(long long)j * n3];
+  RegPlan<N2>::template run<T, -1>(a, tw);
+  const int *sd = sid + ((long long)k * npm + p) * N2;
+  cx<T> *o = i1 + row * nsm * (long long)n3 + j3;
+#pragma unroll
+  for (int j = 0; j < N2; ++j) {
+    int s = __ldg(sd + j);
+    if (s >= 0) o[(long long)s * n3] = a[j];
+  }
+}
+
+template <class T> const cx<T> *tw_of(const AxisPlan &a) {
+  if constexpr (sizeof(T) == 8)
+    return a.tw_d;
+  else
+    return a.tw_f;
+}
+
+inline dim3 grid_rows(unsigned bx, long long rows) {
+  long long y = rows, z = 1;
+  while (y > 65535) {
+    z *= 2;
+    y = (rows + z - 1) / z;
+  }
+  return dim3(bx, (unsigned)y, (unsigned)z);
+}
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes));
+}
+
+constexpr int kTL = 16;
+
+// Register-line transforms: FP32 up to length 48, FP64 up to 45 (spill-free budget).
+template <class T> bool use_reg_lines(int n) {
+  return reg_fft_length(n) && (sizeof(T) == 4 || n <= 45);
+}
+
+}  // namespace
+
+void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
+  const int n1 = s.fft[0], n2 = s.fft[1], n3 = s.fft[2];
+  const int nk = s.nk, npwx = s.npwx;
+  std::vector<std::vector<int>> sticks(nk), planes(nk);
+  std::vector<std::vector<int>> stick_of_cell(nk);  // (j1*n2+j2) -> stick id
+  int nsm = 0, npm = 0;
+  for (int k = 0; k < nk; ++k) {
+    std::vector<int> cell(n1 * n2, -1);
+    std::vector<char> plane_used(n1, 0);
+    for (int g = 0; g < s.npw_kq[k]; ++g) {
+      int id = idx_kq[(size_t)k * npwx + g];
+      int c = id / n3;
+      if (cell[c] < 0) cell[c] = 0;
+      plane_used[c / n2] = 1;
+    }
+    int cnt = 0;
+    for (int c = 0; c < n1 * n2; ++c)
+      if (cell[c] >= 0) {
+        cell[c] = cnt++;
+        sticks[k].push_back(c);
+      }
+    for (int j1 = 0; j1 < n1; ++j1)
+      if (plane_used[j1]) planes[k].push_back(j1);
+    stick_of_cell[k] = cell;
+    nsm = std::max(nsm, cnt);
+    npm = std::max(npm, (int)planes[k].size());
+  }
+  s.nstick_max = nsm;
+  s.nplane_max = npm;
+  std::vector<int> nst(nk), smap((size_t)nk * nsm * n3, -1), npl(nk), plj((size_t)nk * npm, -1),
+      plof((size_t)nk * n1, -1), sid((size_t)nk * npm * n2, -1);
+  for (int k = 0; k < nk; ++k) {
+    nst[k] = (int)sticks[k].size();
+    npl[k] = (int)planes[k].size();
+    for (int g = 0; g < s.npw_kq[k]; ++g) {
+      int id = idx_kq[(size_t)k * npwx + g];
+      int c = id / n3, j3 = id % n3;
+      int st = stick_of_cell[k][c];
+      smap[((size_t)k * nsm + st) * n3 + j3] = g;
+    }
+    for (int p = 0; p < npl[k]; ++p) {
+      int j1 = planes[k][p];
+      plj[(size_t)k * npm + p] = j1;
+      plof[(size_t)k * n1 + j1] = p;
+      for (int j2 = 0; j2 < n2; ++j2)
+        sid[((size_t)k * npm + p) * n2 + j2] = stick_of_cell[k][j1 * n2 + j2];
+    }
+  }
+  auto up = [&](DevBuf &b, const std::vector<int> &v) {
+    b.alloc(v.size() * sizeof(int));
+    TDLZ_CUDA_TRY(cudaMemcpy(b.p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+  };
+  up(s.st_n, nst);
+  up(s.st_map, smap);
+  up(s.pl_n, npl);
+  up(s.pl_j1, plj);
+  up(s.pl_of, plof);
+  up(s.st_id, sid);
+}
+
+template <class T>
+void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *i1, cx<T> *i2,
+                      int nvec) {
+  cudaStream_t st = ctx.stream;
+  const int n1 = s.fft[0], n2 = s.fft[1], n3 = s.fft[2];
+  const long long rows = s.rows() * nvec, n23 = (long long)n2 * n3;
+  const int nsm = s.nstick_max, npm = s.nplane_max;
+  const size_t c = sizeof(cx<T>);
+  {
+    size_t sm = 2ull * n3 * (kTL + 1) * c;
+    set_smem(inv_z_kernel<T, kTL>, sm);
+    inv_z_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+        x, i1, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
+        (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  bool ok = use_reg_lines<T>(n2);
+  if (ok) {
+    dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
+    TDLZ_REG_LAUNCH(n2, inv_y_reg_kernel, g, i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
+                    s.nb, nsm, npm, n3, rows, tw_of<T>(s.plan.ax[1]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  if (!ok) {
+    size_t sm = 2ull * n2 * (kTL + 1) * c;
+    set_smem(inv_y_kernel<T, kTL>, sm);
+    inv_y_kernel<T, kTL><<<grid_rows((n3 + kTL - 1) / kTL, rows * npm), 256, sm, st>>>(
+        i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
+        stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  ok = use_reg_lines<T>(n1);
+  if (ok) {
+    dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
+    TDLZ_REG_LAUNCH(n1, inv_x_reg_kernel, g, i2, xr, s.pl_of.as<int>(), s.nk, s.nb, npm, n23, s.nr,
+                    rows, tw_of<T>(s.plan.ax[0]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  if (!ok) {
+    size_t sm = 2ull * n1 * (kTL + 1) * c;
+    set_smem(inv_x_kernel<T, kTL>, sm);
+    inv_x_kernel<T, kTL><<<grid_rows((unsigned)((n23 + kTL - 1) / kTL), rows), 256, sm, st>>>(
+        i2, xr, s.pl_of.as<int>(), s.nk, s.nb, npm, n1, n23, s.nr, rows, stages(s.plan.ax[0]),
+        tw_of<T>(s.plan.ax[0]));
+    TDLZ_LAUNCH_CHECK();
+  }
+}
+
+template <class T>
+void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, const cx<T> *ur,
+                      const T *vloc, const T *bf, const cx<T> *v, const T *kin, const T *evals,
+                      cx<T> *i1, cx<T> *i2, cx<T> *h, int nvec) {
+  cudaStream_t st = ctx.stream;
+  const int n1 = s.fft[0], n2 = s.fft[1], n3 = s.fft[2];
+  const long long rows = s.rows() * nvec, nbs = rows / 2, n23 = (long long)n2 * n3;
+  const int nsm = s.nstick_max, npm = s.nplane_max;
+  const size_t c = sizeof(cx<T>);
+  bool ok = use_reg_lines<T>(n1);
+  if (ok) {
+    // products in place (xr is not needed afterwards), then the X pass in registers
+    const long long nbs1 = nbs / nvec;
+    product_group_kernel<T><<<grid_rows((unsigned)((s.nr + 255) / 256), nbs1), 256, 0, st>>>(
+        const_cast<cx<T> *>(xr), ur, vloc, bf, v, s.nk, s.nb, s.nr, nvec);
+    TDLZ_LAUNCH_CHECK();
+    dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
+    TDLZ_REG_LAUNCH(n1, fwd_x_reg_kernel, g, xr, i2, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
+                    s.nr, rows, tw_of<T>(s.plan.ax[0]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  if (!ok) {
+    size_t sm = 4ull * n1 * (kTL + 1) * c;
+    set_smem(fwd_x_product_kernel<T, kTL>, sm);
+    fwd_x_product_kernel<T, kTL><<<grid_rows((unsigned)((n23 + kTL - 1) / kTL), nbs), 256, sm,
+                                   st>>>(xr, ur, vloc, bf, v, i2, s.pl_n.as<int>(),
+                                         s.pl_j1.as<int>(), s.nk, s.nb, npm, n1, n23, s.nr, nbs,
+                                         stages(s.plan.ax[0]), tw_of<T>(s.plan.ax[0]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  ok = use_reg_lines<T>(n2);
+  if (ok) {
+    dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
+    TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, g, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
+                    s.nb, nsm, npm, n3, rows, tw_of<T>(s.plan.ax[1]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  if (!ok) {
+    size_t sm = 2ull * n2 * (kTL + 1) * c;
+    set_smem(fwd_y_kernel<T, kTL>, sm);
+    fwd_y_kernel<T, kTL><<<grid_rows((n3 + kTL - 1) / kTL, rows * npm), 256, sm, st>>>(
+        i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
+        stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
+    TDLZ_LAUNCH_CHECK();
+  }
+  {
+    TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * c, st));
+    size_t sm = 2ull * n3 * (kTL + 1) * c;
+    set_smem(fwd_z_gather_kernel<T, kTL>, sm);
+    fwd_z_gather_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+        i1, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm, n3,
+        (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+    TDLZ_LAUNCH_CHECK();
+  }
+}
+
+template void pipeline_inverse<double>(Context &, QSlot &, const double2 *, double2 *, double2 *,
+                                       double2 *, int);
+template void pipeline_inverse<float>(Context &, QSlot &, const float2 *, float2 *, float2 *,
+                                      float2 *, int);
+template void pipeline_forward<double>(Context &, QSlot &, const double2 *, const double2 *,
+                                       const double2 *, const double *, const double *,
+                                       const double2 *, const double *, const double *, double2 *,
+                                       double2 *, double2 *, int);
+template void pipeline_forward<float>(Context &, QSlot &, const float2 *, const float2 *,
+                                      const float2 *, const float *, const float *, const float2 *,
+                                      const float *, const float *, float2 *, float2 *, float2 *,
+                                      int);
+
+}  // namespace tdlz

@@ -35,6 +35,7 @@ __global__ void spectrum_kernel(SpecArgs a) {
   int c = (int)(tid / a.nomega);
   int iw = (int)(tid - (long long)c * a.nomega);
   int m = a.steps[c];
+  if (a.itermax0 > 0 && a.itermax0 < m) m = a.itermax0;
   double2 *out = a.chi + ((long long)c * 3) * a.nomega + iw;
   if (m <= 0) {
     for (int l = 0; l < 3; ++l) out[(long long)l * a.nomega] = make_double2(0, 0);
@@ -46,16 +47,62 @@ __global__ void spectrum_kernel(SpecArgs a) {
   const double2 *zz = a.z + (long long)c * 3 * a.cap;
   double om = a.start + a.step * iw;
   double2 zw = make_double2(om, a.eta);
+  // Extrapolated tail (Sec. 3.3): coefficients m..itermax-1 are the means of the
+  // computed ones over [m/2, m) (per parity for the bi-constant form), z = 0
+  // there; the tail enters through the backward continued fraction g and one
+  // modified diagonal entry d_{m-1} -= beta_{m-1} gamma_{m-1} g.
+  double2 tail = make_double2(0, 0);
+  if (a.extrap != 0 && a.itermax > m && m >= 2) {
+    double2 ca[2] = {{0, 0}, {0, 0}}, cg[2] = {{0, 0}, {0, 0}};
+    double cb[2] = {0, 0};
+    int cnt[2] = {0, 0};
+    for (int j = m / 2; j < m; ++j) {
+      int p = a.extrap == 2 ? (j & 1) : 0;
+      ca[p].x += al[j].x;
+      ca[p].y += al[j].y;
+      cb[p] += be[j];
+      cg[p].x += ga[j].x;
+      cg[p].y += ga[j].y;
+      cnt[p]++;
+    }
+    if (a.extrap != 2) {
+      ca[1] = ca[0];
+      cb[1] = cb[0];
+      cg[1] = cg[0];
+      cnt[1] = cnt[0];
+    }
+    for (int p = 0; p < 2; ++p) {
+      double inv = cnt[p] > 0 ? 1.0 / cnt[p] : 0.0;
+      ca[p] = make_double2(ca[p].x * inv, ca[p].y * inv);
+      cb[p] *= inv;
+      cg[p] = make_double2(cg[p].x * inv, cg[p].y * inv);
+    }
+    double2 g = make_double2(0, 0);
+    for (int j = a.itermax - 1; j >= m; --j) {
+      int p = j & 1;
+      double2 den = make_double2(zw.x - ca[p].x, zw.y - ca[p].y);
+      if (j < a.itermax - 1) {  // - beta_j gamma_j g_{j+1}
+        double2 bg = make_double2(cb[p] * cg[p].x, cb[p] * cg[p].y);
+        den.x -= bg.x * g.x - bg.y * g.y;
+        den.y -= bg.x * g.y + bg.y * g.x;
+      }
+      g = cdiv(make_double2(1.0, 0.0), den);
+    }
+    double2 bg = make_double2(be[m - 1] * ga[m - 1].x, be[m - 1] * ga[m - 1].y);
+    tail = make_double2(bg.x * g.x - bg.y * g.y, bg.x * g.y + bg.y * g.x);
+  }
   // scratch rows (final d, du, du2, b) at [j][tid]
   double2 *sd = a.scratch, *sdu = a.scratch + (long long)a.cap * nthr,
           *sdu2 = a.scratch + 2LL * a.cap * nthr, *sb = a.scratch + 3LL * a.cap * nthr;
   // A = zw - T: d_j = zw - alpha_j, dl_j = -beta_j (A[j+1][j]), du_j = -gamma_j (A[j][j+1])
   double2 d = make_double2(zw.x - al[0].x, zw.y - al[0].y);
+  if (m == 1) d = make_double2(d.x - tail.x, d.y - tail.y);
   double2 du = m > 1 ? make_double2(-ga[0].x, -ga[0].y) : make_double2(0, 0);
   double2 b = make_double2(1.0, 0.0);
   for (int i = 0; i < m - 1; ++i) {
     double2 dl = make_double2(-be[i], 0.0);
     double2 dn = make_double2(zw.x - al[i + 1].x, zw.y - al[i + 1].y);  // d_{i+1}
+    if (i + 1 == m - 1) dn = make_double2(dn.x - tail.x, dn.y - tail.y);
     double2 dun = (i + 1 < m - 1) ? make_double2(-ga[i + 1].x, -ga[i + 1].y) : make_double2(0, 0);
     double2 bn = make_double2(0, 0);
     double2 du2 = make_double2(0, 0);

@@ -14,6 +14,7 @@ struct SpecArgs {
   const double2 *z;      // [nchain][3][cap]
   const double *n0, *wk; // [nchain]
   double start, step, eta;
+  int itermax0, itermax, extrap;  // itermax0 <= 0: all computed; extrap 0 no, 1 constant, 2 osc
   double2 *scratch;      // [4][cap][nchain*nomega]
   double2 *chi;          // [nchain][3][nomega]
 };

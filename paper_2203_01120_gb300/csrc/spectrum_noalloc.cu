@@ -142,6 +142,8 @@ void spectrum_noalloc(Context &ctx, const tdlz_coeffs *c, const tdlz_spectrum_pa
   TDLZ_REQUIRE(sp->step > 0 && sp->end >= sp->start && std::isfinite(sp->eta) && sp->eta > 0,
                TDLZ_ERR_ARG, "need step > 0, end >= start and eta > 0");
   TDLZ_REQUIRE(sp->units == 0 || sp->units == 1, TDLZ_ERR_ARG, "units must be 0 (Ha) or 1 (meV)");
+  TDLZ_REQUIRE(sp->itermax0 == 0 && sp->extrapolation == 0, TDLZ_ERR_ARG,
+               "tdlz_spectrum_noalloc uses every computed step and no extrapolation");
   long long nw = (long long)std::floor((sp->end - sp->start) / sp->step + 0.5) + 1;
   TDLZ_REQUIRE(nw == nomega, TDLZ_ERR_ARG,
                "nomega does not match the frequency grid (query it with tdlz_spectrum, chi = NULL)");

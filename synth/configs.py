@@ -59,6 +59,8 @@ CONFIGS = {
                  seed=1000, alat=6.0),
     "C0K": Config("C0K", _cubic(6.0), (12, 12, 12), 3.6, (1, 2, 1), 4, (0.1, 0, 0), "cubic",
                   seed=1010, alat=6.0),
+    "C0F": Config("C0F", _cubic(6.0), (20, 15, 18), 3.6, (1, 2, 1), 4, (0.1, 0.05, 0), "cubic",
+                  seed=1020, alat=6.0),
     "C1": Config("C1", _cubic(8.0), (16, 16, 16), 5.3, (1, 1, 1), 8, (0.1, 0, 0), "cubic",
                  seed=1001, alat=8.0),
     "C2": Config("C2", _hex(13.0, 30.0), (36, 36, 96), 8.3, (4, 4, 1), 40, (0.125, 0, 0), "hex",
@@ -161,11 +163,13 @@ def _density(coeff, miller, npw, fft, omega, wk):
 def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = False,
                       kernel_mask: int = 3, device: str | None = None, tol: float = 1e-9,
                       ecut: float | None = None, q_2pi_a=None, nocc: int | None = None,
-                      dense_max: int = 2400, log=None) -> GroundState:
+                      dense_max: int = 2400, log=None, solver: str = "auto") -> GroundState:
     """Build the seeded ground-state bundle for config ``name``.
 
     collinear=True gives the special case of a uniform field along z with no
-    spin-orbit coupling ([H, S_z] = 0).
+    spin-orbit coupling ([H, S_z] = 0).  solver="random" skips the
+    diagonalisation and fills the occupied states with random orthonormal
+    spinors (same shapes; for kernel profiling only, not a ground state).
     """
     cfg = dataclasses.replace(CONFIGS[name])
     if seed is not None:
@@ -213,6 +217,7 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
     resid_max = 0.0
     beta_kq = np.zeros((nk, nproj, npwx), dtype=np.complex128)
     torch = None
+    warm = {}
     for ik, k in enumerate(kpts):
         for which, (p, mil) in enumerate(((k, sph_k[ik]), (k + q, sph_kq[ik]))):
             beta = projector_values(p, mil, bvec, omega, atoms)
@@ -220,7 +225,16 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
                 beta_kq[ik, :, :mil.shape[0]] = beta
             npw = mil.shape[0]
             for side, sgn in enumerate((+1, -1)):
-                if 2 * npw <= dense_max:
+                if solver == "random":
+                    # shape-only bundle for kernel profiling: random orthonormal "occupied"
+                    # states and a spread of energies, no diagonalisation
+                    a = rng.standard_normal((2 * npw, nb + 1)) + 1j * rng.standard_normal(
+                        (2 * npw, nb + 1))
+                    v, _ = np.linalg.qr(a)
+                    w = np.linspace(-1.0, 0.0, nb + 1)
+                    w[nb] = 0.5
+                    res = float("nan")
+                elif 2 * npw <= dense_max:
                     h = dense_hamiltonian(sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl)
                     w, v = dense_lowest(h, nb + 1)
                     res = np.linalg.norm(h @ v[:, :nb] - v[:, :nb] * w[None, :nb], axis=0).max()
@@ -233,7 +247,8 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
                     import time as _time
                     _t0 = _time.time()
                     w, v, res = _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield,
-                                           beta, dnl, nb, tol, rng, None)
+                                           beta, dnl, nb, tol, rng, None, warm.get(side))
+                    warm[side] = (mil, v)
                     if log is not None:
                         log(f"  H(k={ik}, {'k+q' if which else 'k'}, side {'XY'[side]}): "
                             f"npw {npw}, resid {res:.1e}, {_time.time() - _t0:.1f} s on {device}")
@@ -266,7 +281,10 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
     return gs
 
 
-def _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl, nb, tol, rng, log):
+def _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl, nb, tol, rng, log,
+               warm=None):
+    """LOBPCG for the lowest nb+1 states; warm = (miller, X) of a neighbouring solve of the
+    same side, mapped onto this sphere by Miller index as the starting block."""
     npw = mil.shape[0]
     h = HamiltonianFFT(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl)
     nev = nb + 1
@@ -274,11 +292,25 @@ def _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl, n
     kin = torch.as_tensor(np.concatenate([0.5 * np.sum((p[None, :] + mil @ bvec) ** 2, 1)] * 2),
                           device=device)
     x0 = np.zeros((2 * npw, m), dtype=np.complex128)
-    order = np.argsort(np.concatenate([np.sum((p[None, :] + mil @ bvec) ** 2, 1)] * 2),
-                       kind="stable")
-    for j in range(m):
-        x0[order[j], j] = 1.0
-    x0 += 0.05 * (rng.standard_normal(x0.shape) + 1j * rng.standard_normal(x0.shape))
+    if warm is not None:
+        wmil, wx = warm
+        key = lambda a: ((a[:, 0].astype(np.int64) + 512) * 1024 + a[:, 1] + 512) * 1024 + a[:, 2] + 512  # noqa: E731
+        wk_, nk_ = key(wmil), key(mil)
+        order_w = np.argsort(wk_)
+        pos = np.searchsorted(wk_[order_w], nk_)
+        pos = np.minimum(pos, len(wk_) - 1)
+        hit = wk_[order_w][pos] == nk_
+        src = order_w[pos[hit]]
+        nw_ = wmil.shape[0]
+        x0[:npw][hit] = wx[:nw_][src]
+        x0[npw:][hit] = wx[nw_:][src]
+        x0 += 1e-3 * (rng.standard_normal(x0.shape) + 1j * rng.standard_normal(x0.shape))
+    else:
+        order = np.argsort(np.concatenate([np.sum((p[None, :] + mil @ bvec) ** 2, 1)] * 2),
+                           kind="stable")
+        for j in range(m):
+            x0[order[j], j] = 1.0
+        x0 += 0.05 * (rng.standard_normal(x0.shape) + 1j * rng.standard_normal(x0.shape))
     x0t = torch.as_tensor(x0, device=device)
 
     def apply_cols(xc):
@@ -286,4 +318,5 @@ def _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl, n
         return h(xb).reshape(xc.shape[1], 2 * npw).T
 
     theta, x, res = lobpcg(torch, apply_cols, kin, x0t, nev, tol=tol, log=log)
-    return theta.cpu().numpy(), x.cpu().numpy(), float(res[:nb].max())
+    xn = x.cpu().numpy()
+    return theta.cpu().numpy(), xn, float(res[:nb].max())

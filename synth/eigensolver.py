@@ -17,12 +17,18 @@ def dense_lowest(h: np.ndarray, nev: int):
     return w[:nev], v[:, :nev]
 
 
+def _eigh_small(t, a):
+    """Eigen-decomposition of a small Hermitian matrix on the host (GPU eigh is slow here)."""
+    w, v = t.linalg.eigh(0.5 * (a + a.conj().T).cpu())
+    return w.to(a.device), v.to(a.device)
+
+
 def _orthonormal(t, s, drop=1e-10):
     """Orthonormal basis of span(s) (eigen-decomposition of the scaled Gram matrix)."""
     g = s.conj().T @ s
     d = t.rsqrt(t.clamp(t.real(t.diagonal(g)), min=1e-300))
     g = d[:, None] * g * d[None, :]
-    lam, v = t.linalg.eigh(0.5 * (g + g.conj().T))
+    lam, v = _eigh_small(t, g)
     keep = lam > drop * lam.max()
     return s @ ((d[:, None] * v[:, keep]) * t.rsqrt(lam[keep])[None, :])
 
@@ -40,7 +46,7 @@ def lobpcg(t, apply_h, kin, x0, nconv, tol=1e-9, maxiter=400, log=None):
     x = _orthonormal(t, x0)
     hx = apply_h(x)
     a = x.conj().T @ hx
-    theta, c = t.linalg.eigh(0.5 * (a + a.conj().T))
+    theta, c = _eigh_small(t, a)
     x, hx = x @ c, hx @ c
     p = None
     e_ref = max(1.0, float(t.mean(kin)))
@@ -62,7 +68,7 @@ def lobpcg(t, apply_h, kin, x0, nconv, tol=1e-9, maxiter=400, log=None):
         hz = apply_h(z)
         s, hs = t.cat([x, z], 1), t.cat([hx, hz], 1)
         a = s.conj().T @ hs
-        th, c = t.linalg.eigh(0.5 * (a + a.conj().T))
+        th, c = _eigh_small(t, a)
         p = z @ c[m:, :m]
         x, hx, theta = s @ c[:, :m], hs @ c[:, :m], th[:m]
     hx = apply_h(x)

@@ -59,7 +59,7 @@ def apply_gpu(torch, ctx, q, x, adjoint=False, mixed=False):
 
 
 @pytest.mark.parametrize("name,mask", [("C0", 3), ("C0K", 0), ("C0K", 1), ("C0K", 2), ("C0K", 3),
-                                       ("C1", 3)])
+                                       ("C0F", 3), ("C1", 3)])
 def test_apply_fp64(torch, ctx, name, mask):
     q = slot(ctx, name, mask)
     lv = liouvillian(name, mask)
@@ -82,7 +82,7 @@ def test_apply_adjoint_fp64(torch, ctx):
     assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("name", ["C0K", "C1"])
+@pytest.mark.parametrize("name", ["C0K", "C0F", "C1"])
 def test_apply_mixed(torch, ctx, name):
     q = slot(ctx, name)
     lv = liouvillian(name)
@@ -169,3 +169,69 @@ def test_invalid_inputs_rejected(torch, ctx):
     x = __import__("torch").zeros(10, dtype=__import__("torch").complex128, device="cuda")
     with pytest.raises(TdlzError):
         ctx.apply_liouvillian(q, x, x)  # overlapping x, y
+
+
+@pytest.mark.parametrize("flavor", ["nh", "phm"])
+def test_grouped_chains_equal_single_chains(torch, ctx, flavor):
+    """Chains of one q-slot advance in one stacked Liouvillian pass; each must match
+    the same chain run alone (C1, FP64, 20 steps)."""
+    q = slot(ctx, "C1")
+    grouped = ctx.lanczos_run([q, q, q], [0, 1, 2], 20, flavor)
+    for c in range(3):
+        alone = ctx.lanczos_run([q], [c], 20, flavor)
+        for key in ("alpha", "beta", "gamma", "z"):
+            a, b = grouped[key][c], alone[key][0]
+            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), (c, key)
+
+
+@pytest.mark.parametrize("kind", ["constant", "osc"])
+def test_spectrum_extrapolation_matches_oracle(torch, ctx, kind):
+    """Extrapolated chi (itermax0 = 30 computed, itermax = 2000) against the oracle's
+    explicitly extended system."""
+    from oracle.lanczos import Coefficients
+    from oracle.spectrum import chi_extrapolated, omega_grid_mev, HA_MEV
+    q = slot(ctx, "C1")
+    got = ctx.lanczos_run([q], [0], 40, "nh")
+    chi = ctx.spectrum(got, 0.0, 1000.0, 2.0, 10.0, units=1, itermax0=30, itermax=2000,
+                       extrapolation=kind)[0]
+    co = Coefficients(got["alpha"][0], got["beta"][0], got["gamma"][0], got["z"][0],
+                      got["n0"][0], int(got["steps_done"][0]), "ok")
+    om = omega_grid_mev(0.0, 1000.0, 2.0) / HA_MEV
+    ref = chi_extrapolated(co, om, 10.0 / HA_MEV, got["wk"][0], 30, 2000, kind)
+    assert np.max(np.abs(chi - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("flavor,prec", [("nh", 0), ("phm", 0), ("nh", 1), ("ph", 1)])
+def test_restart_resumes_bitwise(torch, ctx, flavor, prec):
+    """Save after 12 steps, restore into a fresh chain set of larger capacity,
+    continue to 30: identical coefficients to an uninterrupted 30-step run."""
+    q = slot(ctx, "C1")
+    straight = ctx.lanczos_run([q, q], [0, 2], 30, flavor, prec)
+    a = ctx.chain_create([q, q], [0, 2], 12, flavor, prec)
+    a.advance(12)
+    image = a.save()
+    a.close()
+    b = ctx.chain_create([q, q], [0, 2], 30, flavor, prec)
+    b.restore(image)
+    b.advance(18)
+    resumed = b.read()
+    b.close()
+    for key in ("alpha", "beta", "gamma", "z", "n0", "steps_done", "status"):
+        assert np.array_equal(resumed[key], straight[key]), key
+
+
+def test_restart_rejects_mismatched_image(torch, ctx):
+    from paper_2203_01120_gb300 import TdlzError
+    q = slot(ctx, "C1")
+    a = ctx.chain_create([q], [0], 5, "nh")
+    a.advance(2)
+    image = a.save()
+    a.close()
+    b = ctx.chain_create([q], [1], 5, "nh")  # different mu
+    with pytest.raises(TdlzError):
+        b.restore(image)
+    b.close()
+    c = ctx.chain_create([q], [0], 3, "nh")  # smaller capacity
+    with pytest.raises(TdlzError):
+        c.restore(image)
+    c.close()

@@ -243,3 +243,52 @@ def test_p9_sum_rule():
     om = np.linspace(-r, r, 160001)
     integ = np.trapezoid(chi_thomas(c, om, eta, w), om, axis=1)
     assert abs(integ[0] + 2.0 * first / r - exact[0]) <= 1e-4 * abs(exact[0])
+
+
+def _terminator_chi(coef, omegas, eta, w, itermax0, itermax, kind):
+    """The extrapolated tail folded into the last computed diagonal entry by its
+    backward continued fraction (what the GPU spectrum kernel evaluates)."""
+    from oracle.spectrum import extrapolation_constants
+    c = extrapolation_constants(coef, itermax0, kind)
+    out = np.zeros((3, len(omegas)), dtype=np.complex128)
+    for i, om in enumerate(omegas):
+        zz = om + 1j * eta
+        g = 0.0
+        for j in range(itermax - 1, itermax0 - 1, -1):
+            a, b, gm = c[j % 2]
+            link = (b.real * gm) if j < itermax - 1 else 0.0
+            g = 1.0 / (zz - a - link * g)
+        m = itermax0
+        d = zz - coef.alpha[:m].astype(complex)
+        d[m - 1] -= coef.beta[m - 1] * coef.gamma[m - 1] * g
+        ab = np.zeros((3, m), dtype=np.complex128)
+        ab[0, 1:] = -coef.gamma[:m - 1]
+        ab[1] = d
+        ab[2, :-1] = -coef.beta[:m - 1]
+        e1 = np.zeros(m, dtype=np.complex128)
+        e1[0] = 1
+        x = __import__("scipy.linalg").linalg.solve_banded((1, 1), ab, e1)
+        out[:, i] = w * coef.n0 * (coef.z[:, :m].conj() @ x)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["constant", "osc"])
+def test_extrapolation_terminator_equals_extended_system(c0_chains, kind):
+    """Folding the extrapolated tail into one diagonal entry (continued fraction)
+    equals solving the explicitly extended system; 'no' equals truncation."""
+    from oracle.spectrum import chi_extrapolated, extend_coefficients
+    lv = liouvillian("C0")
+    c = c0_chains["nh"][0]
+    w = lv.gs.wk[0]
+    eta = 10.0 / HA_MEV
+    ref = chi_extrapolated(c, OMEGAS, eta, w, 60, 400, kind)
+    got = _terminator_chi(c, OMEGAS, eta, w, 60, 400, kind)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    ext = extend_coefficients(c, 60, 400, kind)
+    assert ext.steps == 400 and not ext.z[:, 60:].any()
+    if kind == "constant":
+        assert np.allclose(ext.beta[60:], ext.beta[60]) and np.allclose(ext.alpha[60:], ext.alpha[60])
+    else:
+        assert np.allclose(ext.beta[60::2], ext.beta[60]) and np.allclose(ext.beta[61::2], ext.beta[61])
+    trunc = chi_extrapolated(c, OMEGAS, eta, w, 60, 400, "no")
+    assert np.allclose(trunc, chi_banded(c, OMEGAS, eta, w, m=60), rtol=1e-12, atol=0)
