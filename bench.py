@@ -238,10 +238,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, profile=False):
+def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, stream, profile=False):
     """Chain-steps per second summed over the chains mus (one group on one q-slot).
-    The library runs on its own stream; the timed region is bracketed by
-    synchronisations of that stream (tdlz_synchronize) on both sides."""
+    The library runs on `stream` (handed to it at context creation); the timed
+    region is bracketed by CUDA events recorded on that stream, with the stream
+    synchronised on both sides."""
+    import torch
     ch = ctx.chain_create([q] * len(mus), mus, warmup + steps + 1, flavor, precision)
     try:
         ch.advance(warmup)
@@ -249,11 +251,14 @@ def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, profile=Fal
         if profile:
             ctx.profile(True)
         l0 = ctx.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         ctx.synchronize()
-        t0 = time.perf_counter()
+        ev0.record(stream)
         ch.advance(steps)
+        ev1.record(stream)
         ctx.synchronize()
-        wall = time.perf_counter() - t0
+        wall = ev0.elapsed_time(ev1) / 1000.0
         launches = ctx.launch_count() - l0
         prof = ctx.profile_read() if profile else None
         if profile:
@@ -277,7 +282,8 @@ def run_tdlz(args):
     gs = make_workload(args.config, args.tol, args.bundle)
     # replicas: every rank runs the chi columns mus (the paper's ipol = 4: x, y, z)
     mus = list(range(args.chains))
-    ctx = Context(local)
+    stream = torch.cuda.Stream(device=local)
+    ctx = Context(local, stream=stream.cuda_stream)
     # ------------------------------------------------------------ e2e (host in/out)
     t0 = time.perf_counter()
     q = ctx.load_ground_state(gs)
@@ -296,15 +302,15 @@ def run_tdlz(args):
     clk = ClockSampler(local)
     clk.start()
     sps_mixed, wall_mixed, launches, _, _ = chain_steps_per_s(
-        ctx, q, mus, args.flavor, TDLZ_MIXED, args.warmup, args.steps)
+        ctx, q, mus, args.flavor, TDLZ_MIXED, args.warmup, args.steps, stream)
     clocks = clk.finish()
     wall_mixed = max_over_ranks(wall_mixed, "cuda")
     # profiled pass (per-stage CUDA events on the library stream) for the roofline
     _, _, _, prof, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_MIXED, 1, args.steps,
-                                         profile=True)
+                                         stream, profile=True)
     fp64_steps = max(3, args.steps // 4)
     sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_FP64, 1,
-                                                          fp64_steps, profile=True)
+                                                          fp64_steps, stream, profile=True)
     # ------------------------------------------------------------ chi error mixed vs FP64
     m = args.chi_steps
     r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)

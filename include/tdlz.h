@@ -178,7 +178,12 @@ tdlz_status tdlz_apply_liouvillian(tdlz_ctx *ctx, int qslot, const void *x, void
 /* Chains that advance on the device without host round trips; the
  * coefficients stay on the device until tdlz_chain_read. */
 tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_chain **out);
-tdlz_status tdlz_chain_advance(tdlz_chain *ch, int nsteps); /* enqueue nsteps steps */
+/* Enqueue nsteps steps.  From four steps on, pairs of steps are replayed from a
+ * CUDA graph recorded on the context stream at the first such call (the graph is
+ * re-recorded when the chain's vector rotation differs from the recorded one);
+ * results are identical to eager steps.  The caller must not capture the context
+ * stream around this call.  With profiling on, every step runs eagerly. */
+tdlz_status tdlz_chain_advance(tdlz_chain *ch, int nsteps);
 tdlz_status tdlz_chain_read(tdlz_chain *ch, tdlz_lanczos_result *res); /* synchronises */
 void tdlz_chain_destroy(tdlz_chain *ch);
 
@@ -228,6 +233,17 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
 #define TDLZ_NOALLOC_SCRATCH_MB 32
 tdlz_status tdlz_spectrum_noalloc(tdlz_ctx *ctx, const tdlz_coeffs *dev_coeffs,
                                   const tdlz_spectrum_params *sp, double *dev_chi, int nomega);
+
+/* Neutron-scattering structure factor S(q, omega) = -Im Tr[P_perp(q) chi(q, q; omega)]
+ * with P_perp_ab = delta_ab - q_a q_b / q^2 (Eqs. cross_section and S_def, Sec. 2.1).
+ * chi: caller-owned HOST array [3][3][nomega] complex double (interleaved re, im),
+ * chi[mu][lambda][w] = chi_{lambda mu}(omega_w): the tdlz_spectrum rows of the three
+ * chains mu = x, y, z of one q-slot, stacked in that order.
+ * q[3]: the transferred momentum (Cartesian; only its direction enters).
+ * S: caller-owned HOST array [nomega].  Computed on the context's device;
+ * synchronises.  TDLZ_ERR_ARG for NULL pointers, nomega < 1 or q = 0. */
+tdlz_status tdlz_structure_factor(tdlz_ctx *ctx, const double *chi, int nomega,
+                                  const double *q, double *S);
 
 /* ---- measurement (no counterpart in the paper, whose own numbers are wall
  * times only): per-stage device time from CUDA events recorded on the context

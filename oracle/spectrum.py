@@ -139,3 +139,17 @@ def chi_extrapolated(coef, omegas, eta, w, itermax0, itermax, kind):
     """chi from the explicitly extended tridiagonal system (pivoted banded solve)."""
     ext = extend_coefficients(coef, itermax0, itermax, kind)
     return chi_banded(ext, omegas, eta, w)
+
+
+def structure_factor(chi3, q):
+    """S(q, omega) = -Im Tr[P_perp(q) chi(q, q; omega)] (Eq. S_def, Sec. 2.1), with
+    P_perp_ab = delta_ab - q_a q_b / q^2 and chi3[mu][lambda][w] = chi_{lambda mu}(w)
+    (the chi rows of the chains mu = x, y, z).  Tr[P chi] = sum_ab P_ab chi_ba."""
+    q = np.asarray(q, dtype=np.float64)
+    p = np.eye(3) - np.outer(q, q) / (q @ q)
+    chi3 = np.asarray(chi3, dtype=np.complex128)
+    s = np.zeros(chi3.shape[-1], dtype=np.complex128)
+    for a in range(3):
+        for b in range(3):
+            s += p[a, b] * chi3[a, b]  # chi_ba is row b of chain a
+    return -s.imag

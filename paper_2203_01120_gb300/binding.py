@@ -88,6 +88,7 @@ EXPORTS = {
                                 C.POINTER(TdlzSpectrumParams), _dp, _ip]),
     "tdlz_spectrum_noalloc": (C.c_int, [C.c_void_p, C.POINTER(TdlzCoeffs),
                                         C.POINTER(TdlzSpectrumParams), C.c_void_p, C.c_int]),
+    "tdlz_structure_factor": (C.c_int, [C.c_void_p, _dp, C.c_int, _dp, _dp]),
     "tdlz_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "tdlz_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), _dp, _dp]),
     "tdlz_stage_name": (C.c_char_p, [C.c_int]),
@@ -283,6 +284,18 @@ class Context:
         self._check(self.lib.tdlz_spectrum_noalloc(self.h, C.byref(c), C.byref(sp),
                                                    C.c_void_p(chi_dev.data_ptr()),
                                                    int(chi_dev.shape[-1])))
+
+    def structure_factor(self, chi3, q):
+        """S(q, omega) = -Im Tr[P_perp(q) chi] from chi3[mu][lambda][nomega] (complex)."""
+        chi3 = np.ascontiguousarray(chi3, dtype=np.complex128)
+        if chi3.ndim != 3 or chi3.shape[:2] != (3, 3):
+            raise ValueError("chi3 must be [3][3][nomega]")
+        nw = chi3.shape[2]
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros(nw, dtype=np.float64)
+        self._check(self.lib.tdlz_structure_factor(self.h, _dptr(chi3.view(np.float64)), int(nw),
+                                                   _dptr(qq), _dptr(out)))
+        return out
 
     def spectrum_nomega(self, start, end, step, units=1):
         """Frequency-grid length (tdlz_spectrum with chi = NULL; allocates nothing)."""

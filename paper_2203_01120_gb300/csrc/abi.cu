@@ -3,12 +3,14 @@
 // tdlz_status with a message for tdlz_last_error(); no C++ exception crosses
 // the boundary.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "lanczos.cuh"
 #include "spectrum.cuh"
+#include "tc_gemm.cuh"
 
 using namespace tdlz;
 
@@ -128,12 +130,36 @@ tdlz_status tdlz_spectrum_noalloc(tdlz_ctx *ctx, const tdlz_coeffs *dev_coeffs,
   return guarded(ctx, [&] { spectrum_noalloc(ctx->c, dev_coeffs, sp, dev_chi, nomega); });
 }
 
+tdlz_status tdlz_structure_factor(tdlz_ctx *ctx, const double *chi, int nomega,
+                                  const double *q, double *S) {
+  return guarded(ctx, [&] {
+    TDLZ_REQUIRE(chi && q && S, TDLZ_ERR_ARG, "NULL chi, q or S");
+    TDLZ_REQUIRE(nomega >= 1, TDLZ_ERR_ARG, "nomega must be >= 1");
+    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    TDLZ_REQUIRE(std::isfinite(q2) && q2 > 0, TDLZ_ERR_ARG, "q must be a finite non-zero vector");
+    PerpProj p;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) p.m[a][b] = (a == b ? 1.0 : 0.0) - q[a] * q[b] / q2;
+    cudaStream_t st = ctx->c.stream;
+    DevBuf dchi, dS;
+    dchi.alloc((size_t)9 * nomega * sizeof(double2));
+    dS.alloc((size_t)nomega * sizeof(double));
+    TDLZ_CUDA_TRY(cudaMemcpyAsync(dchi.p, chi, dchi.bytes, cudaMemcpyHostToDevice, st));
+    launch_structure_factor(st, dchi.as<double2>(), nomega, p, dS.as<double>());
+    TDLZ_CUDA_TRY(cudaMemcpyAsync(S, dS.p, dS.bytes, cudaMemcpyDeviceToHost, st));
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
 const char *tdlz_stage_name(int stage) { return stage_name(stage); }
 
 int64_t tdlz_launch_count(void) { return g_launches.load(); }
 
 tdlz_status tdlz_synchronize(tdlz_ctx *ctx) {
-  return guarded(ctx, [&] { TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream)); });
+  return guarded(ctx, [&] {
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+    tc_gemm_check();
+  });
 }
 
 tdlz_status tdlz_load_ground_state(tdlz_ctx *ctx, const tdlz_ground_state *gs, int *qslot) {
@@ -203,6 +229,9 @@ tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_
     ch->set.flavor = p->flavor;
     ch->set.precision = p->precision;
     ch->set.cap = p->nsteps;
+    // TDLZ_GRAPHS=0 keeps every step eager (A/B timing of the graph replay)
+    const char *ge = std::getenv("TDLZ_GRAPHS");
+    ch->set.use_graphs = !(ge && ge[0] == '0');
     ch->set.chains.resize(p->nchain);
     for (int c = 0; c < p->nchain; ++c) {
       ch->set.chains[c].qslot = p->qslot[c];

@@ -69,6 +69,7 @@ template <class T> struct SlotData {
   DevBuf vhfac;  // [Nr]   4 pi / |q+G|^2 / Nr on the Hartree sphere (real)
   DevBuf wk;     // [nk]   (real)
   DevBuf uvec;   // [3][BR] u^lambda = J sigma^lambda U (unprojected)
+  DevBuf us;     // FP32 slab path: [2][nk][nb][2][n3][n1*n2 (even)] U(r) in z-major slabs
   bool ready = false;
 };
 
@@ -86,6 +87,7 @@ template <class T> struct Workspace {
   DevBuf part;  // split-K partial sums
   DevBuf i1;    // [rows][nstick_max][n3] stick scratch
   DevBuf i2;    // [rows][nplane_max][n2][n3] plane scratch
+  DevBuf coef;  // slab path: [nvec][2][6][Nr] complex product-coefficient planes
   int nvec_cap = 0;  // stacked vectors the buffers above are sized for
   bool ready = false;
 };
@@ -110,6 +112,8 @@ struct QSlot {
   DevBuf pl_j1;   // [nk][nplane_max] grid index j1 of each plane
   DevBuf pl_of;   // [nk][n1] plane index of j1 or -1
   DevBuf st_id;   // [nk][nplane_max][n2] stick index of (plane, j2) or -1
+  bool slab = false;  // FP32 Liouvillian runs the plane-slab real-space stages (slab.cu)
+  bool tensor_gemm = true;  // FP32 V_NL / P_c reductions on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;
   SlotData<float> d32;

@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "lanczos.cuh"
+#include "tc_gemm.cuh"
 
 namespace tdlz {
 
@@ -554,15 +555,89 @@ void ChainSet::init() {
     init_impl<float>();
 }
 
-void ChainSet::advance(int nsteps) {
+void ChainSet::advance_eager(int nsteps) {
+  if (nsteps <= 0) return;
   if (precision == TDLZ_FP64)
     advance_impl<double>(nsteps);
   else
     advance_impl<float>(nsteps);
 }
 
+ChainSet::~ChainSet() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+}
+
+std::vector<void *> ChainSet::slot_key() const {
+  std::vector<void *> k;
+  for (const Group &g : groups)
+    for (int i = 0; i < 4; ++i) k.push_back(g.slot[i]);
+  return k;
+}
+
+// Records two steps of every group into a graph without running them: the host
+// bookkeeping that the recording advanced (step counters, launch counter) is put
+// back, and the slot pointers are back where they were after two rotations.
+void ChainSet::capture_two_steps() {
+  if (gexec) {
+    cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+  std::vector<int> steps;
+  for (const Group &g : groups) steps.push_back(g.host_step);
+  const long long l0 = g_launches.load();
+  cudaStream_t st = ctx->stream;
+  TDLZ_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  cudaGraph_t graph = nullptr;
+  try {
+    advance_eager(2);
+  } catch (...) {
+    cudaStreamEndCapture(st, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    for (size_t i = 0; i < groups.size(); ++i) groups[i].host_step = steps[i];
+    throw;
+  }
+  TDLZ_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+  graph_kernels = g_launches.load() - l0;
+  g_launches.fetch_sub(graph_kernels);
+  for (size_t i = 0; i < groups.size(); ++i) groups[i].host_step = steps[i];
+  cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    gexec = nullptr;
+    throw Error{TDLZ_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+  }
+  graph_key = slot_key();
+}
+
+// Steps run eagerly (one launch sequence per step) while the profiler records
+// per-stage events or while fewer than four steps are asked for; otherwise one
+// eager step (which also sizes every workspace), then pairs of steps replayed
+// from the captured graph, then the remainder eagerly.
+void ChainSet::advance(int nsteps) {
+  if (!use_graphs || ctx->prof.on || nsteps < 4) {
+    advance_eager(nsteps);
+    return;
+  }
+  advance_eager(1);
+  int done = 1;
+  int room = nsteps - done;
+  for (const Group &g : groups) room = std::min(room, cap - g.host_step);
+  const int pairs = room / 2;
+  if (pairs > 0) {
+    if (!gexec || graph_key != slot_key()) capture_two_steps();
+    for (int p = 0; p < pairs; ++p) {
+      TDLZ_CUDA_TRY(cudaGraphLaunch(gexec, ctx->stream));
+      g_launches.fetch_add(graph_kernels);
+    }
+    for (Group &g : groups) g.host_step += 2 * pairs;
+    done += 2 * pairs;
+  }
+  advance_eager(nsteps - done);
+}
+
 void ChainSet::read(tdlz_lanczos_result *res) {
   TDLZ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  tc_gemm_check();
   for (size_t c = 0; c < chains.size(); ++c) {
     Chain &ch = chains[c];
     ChainScalars hs;

@@ -46,6 +46,13 @@ struct ChainSet {
   std::vector<Chain> chains;
   std::vector<Group> groups;
   DevBuf red;
+  // Two steps captured as one CUDA graph (the vector-slot rotation has period 2) and
+  // replayed; valid while the slot arrangement equals the captured one.
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<void *> graph_key;  // slot pointers of every group at capture
+  long long graph_kernels = 0;    // kernels in the captured graph
+  bool use_graphs = true;
+  ~ChainSet();
   void init();
   void advance(int nsteps);
   void read(tdlz_lanczos_result *res);
@@ -58,6 +65,9 @@ struct ChainSet {
  private:
   template <class T> void init_impl();
   template <class T> void advance_impl(int nsteps);
+  void advance_eager(int nsteps);
+  std::vector<void *> slot_key() const;
+  void capture_two_steps();
 };
 
 }  // namespace tdlz

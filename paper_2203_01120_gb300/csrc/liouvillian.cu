@@ -14,11 +14,14 @@
 //   7  V_NL: <beta|x> (split-K reduction GEMM), D mixing, beta (D <beta|x>)
 //   8  P_c: <U_m|h> (split-K reduction GEMM), h - U <U|h>, row sign (Y side -)
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 
 #include "engine.cuh"
 #include "pipeline.cuh"
+#include "slab.cuh"
+#include "tc_gemm.cuh"
 
 namespace tdlz {
 
@@ -59,9 +62,10 @@ inline dim3 row_grid(long long nrows, int npwx) {
 // Block row y sums the (side, k) pairs [y*ppg, (y+1)*ppg) into partial slice y
 // ([gridDim.y][nvec][4][Nr]); density_reduce_kernel adds the slices in order.
 template <class T, int NV>
-__global__ void density_kernel(const cx<T> *__restrict__ ur, const cx<T> *__restrict__ xr,
-                               const T *__restrict__ wk, cx<T> *__restrict__ rho, int nk, int nb,
-                               long long nr, int nvec, int ppg, int vstride) {
+__global__ void __launch_bounds__(256)
+    density_kernel(const cx<T> *__restrict__ ur, const cx<T> *__restrict__ xr,
+                   const T *__restrict__ wk, cx<T> *__restrict__ rho, int nk, int nb,
+                   long long nr, int ppg, int vstride) {
   const long long rows1 = 4LL * nk * nb;
   const int pb = blockIdx.y * ppg, pe = min(2 * nk, pb + ppg);
   rho += (long long)blockIdx.y * vstride * 4 * nr;
@@ -70,45 +74,43 @@ __global__ void density_kernel(const cx<T> *__restrict__ ur, const cx<T> *__rest
     cx<T> acc[NV][4];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
+#pragma unroll
       for (int a = 0; a < 4; ++a) acc[v][a] = czero<T>();
     for (int pair = pb; pair < pe; ++pair) {
       const int side = pair / nk, k = pair - side * nk;
-      T t = side == 0 ? T(1) : T(-1);
-      {
-        cx<T> a[NV][4];
+      const T w = wk[k], wt = side == 0 ? w : -w;
+      cx<T> a[NV][4];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          for (int c = 0; c < 4; ++c) a[v][c] = czero<T>();
-        for (int n = 0; n < nb; ++n) {
-          long long row = (((long long)side * nk + k) * nb + n) * 2;
-          cx<T> u0 = ur[row * nr + r], u1 = ur[(row + 1) * nr + r];
+      for (int v = 0; v < NV; ++v)
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            if (v >= nvec) break;
-            long long rv = row + v * rows1;
-            cx<T> x0 = xr[rv * nr + r], x1 = xr[(rv + 1) * nr + r];
-            cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
-            cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
-            a[v][0] = cadd<T>(a[v][0], cadd<T>(p00, p11));
-            a[v][1] = cadd<T>(a[v][1], cadd<T>(p01, p10));
-            cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
-            a[v][2] = cadd<T>(a[v][2], mk<T>(-d.y, d.x));
-            a[v][3] = cadd<T>(a[v][3], csub<T>(p00, p11));
-          }
+        for (int c = 0; c < 4; ++c) a[v][c] = czero<T>();
+      for (int n = 0; n < nb; ++n) {
+        const long long row = ((long long)pair * nb + n) * 2;
+        const cx<T> u0 = __ldg(ur + row * nr + r), u1 = __ldg(ur + (row + 1) * nr + r);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {  // every vector of the pass: no early exit, so
+          const long long rv = row + v * rows1;  // all loads of a band issue together
+          const cx<T> x0 = xr[rv * nr + r], x1 = xr[(rv + 1) * nr + r];
+          const cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
+          const cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
+          a[v][0] = cadd<T>(a[v][0], cadd<T>(p00, p11));
+          a[v][1] = cadd<T>(a[v][1], cadd<T>(p01, p10));
+          const cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
+          a[v][2] = cadd<T>(a[v][2], mk<T>(-d.y, d.x));
+          a[v][3] = cadd<T>(a[v][3], csub<T>(p00, p11));
         }
-        T w = wk[k];
+      }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          acc[v][0] = cadd<T>(acc[v][0], cscale<T>(a[v][0], w));
-          for (int c = 1; c < 4; ++c) acc[v][c] = cadd<T>(acc[v][c], cscale<T>(a[v][c], w * t));
-        }
+      for (int v = 0; v < NV; ++v) {
+        acc[v][0] = cadd<T>(acc[v][0], cscale<T>(a[v][0], w));
+#pragma unroll
+        for (int c = 1; c < 4; ++c) acc[v][c] = cadd<T>(acc[v][c], cscale<T>(a[v][c], wt));
       }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      if (v >= nvec) break;
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
       for (int a = 0; a < 4; ++a) rho[((long long)v * 4 + a) * nr + r] = acc[v][a];
-    }
   }
 }
 
@@ -138,13 +140,15 @@ void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *
   const int ng = (npair + ppg - 1) / ppg;
   const dim3 grid(blocks_for(nr), ng);
   for (int v0 = 0; v0 < nvec; v0 += 3) {
-    int nv = std::min(3, nvec - v0);
+    const int nv = std::min(3, nvec - v0);
     const cx<T> *xv = xr + (long long)v0 * rows1 * nr;
     cx<T> *pv = part + (long long)v0 * 4 * nr;
     if (nv == 1)
-      density_kernel<T, 1><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, 1, ppg, nvec);
+      density_kernel<T, 1><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
+    else if (nv == 2)
+      density_kernel<T, 2><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
     else
-      density_kernel<T, 3><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, nv, ppg, nvec);
+      density_kernel<T, 3><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
     TDLZ_LAUNCH_CHECK();
   }
   long long n = (long long)nvec * 4 * nr;
@@ -153,22 +157,6 @@ void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *
 }
 
 // --------------------------------------------------------- Hartree + ALSDA
-template <class T>
-__global__ void copy_scale_kernel(const cx<T> *__restrict__ a, cx<T> *__restrict__ b,
-                                  const T *__restrict__ fac, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = fac ? cscale<T>(a[i], fac[i]) : a[i];
-}
-
-template <class T>
-__global__ void scale_inplace_kernel(cx<T> *__restrict__ a, const T *__restrict__ fac,
-                                     long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    a[i] = cscale<T>(a[i], fac[i]);
-}
-
 // v_a = delta_a0 vH + sum_b f_ab rho_b ; f packed 00,01,02,03,11,12,13,22,23,33
 template <class T>
 __global__ void potential_kernel(const cx<T> *__restrict__ rho, const cx<T> *__restrict__ vh,
@@ -495,6 +483,7 @@ void alloc_workspace(QSlot &s, int nvec) {
   if (w.ready && w.nvec_cap >= nvec) return;
   const size_t c = sizeof(cx<T>), nv = (size_t)nvec;
   w.ready = false;
+  const bool slab = sizeof(T) == 4 && s.slab;  // plane-slab path: no plane buffer
   w.xr.alloc(nv * s.rows() * s.nr * c);
   w.rho.alloc(nv * 4 * (size_t)s.nr * c);
   w.rhopart.alloc((size_t)kDensityGroups * nv * 4 * (size_t)s.nr * c);
@@ -510,7 +499,12 @@ void alloc_workspace(QSlot &s, int nvec) {
   size_t p2 = (size_t)32 * batch * s.nb * s.nb;
   w.part.alloc(std::max(p1, p2) * c);
   w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
-  w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+  if (slab) {
+    w.i2.reset();
+    w.coef.alloc(nv * 2 * 6 * (size_t)s.nr * sizeof(float2));
+  } else {
+    w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+  }
   w.nvec_cap = nvec;
   w.ready = true;
 }
@@ -692,6 +686,13 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   };
   s.plan.init(gs->fft);
   build_stick_tables(s, idx_kq);
+  // TDLZ_SLAB=1 selects the plane-slab real-space stages (fused Y+X passes) where the
+  // grid allows them; the staged pipeline is the default
+  const char *slab_env = std::getenv("TDLZ_SLAB");
+  s.slab = slab_supported(s) && slab_env && slab_env[0] == '1';
+  // TDLZ_TC=0 keeps the V_NL / P_c reductions on the CUDA-core GEMM (A/B timing)
+  const char *tc_env = std::getenv("TDLZ_TC");
+  s.tensor_gemm = !(tc_env && tc_env[0] == '0');
   up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
   up(s.idx_kq, idx_kq.data(), idx_kq.size() * sizeof(int));
   up(s.map_kq_k, map.data(), map.size() * sizeof(int));
@@ -744,7 +745,10 @@ void ensure_precision(Context &ctx, QSlot &s) {
     if (!f.ready) {
       SlotData<double> &d = s.d64;
       convert_buf<float>(ctx, d.ukq, f.ukq);
-      convert_buf<float>(ctx, d.ur, f.ur);
+      if (s.slab)
+        slab_build_u(ctx, s, d.ur.as<double2>(), f.us);
+      else
+        convert_buf<float>(ctx, d.ur, f.ur);
       if (s.nproj > 0) {
         convert_buf<float>(ctx, d.beta, f.beta);
         convert_buf<float>(ctx, d.dnl, f.dnl);
@@ -777,7 +781,8 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   const int nk = s.nk, nb = s.nb, npwx = s.npwx, np_ = s.nproj;
   const long long nr = s.nr, rows = s.rows() * nvec, nbs = rows / 2, br = s.br_elems();
   const int batch1 = 2 * nk, batch = batch1 * nvec;
-  // algorithmic traffic / work per stage (see the design doc for the definitions)
+  // algorithmic traffic / work per stage: the bytes each stage must move at minimum for
+  // its design and its nominal flops, accumulated by the profiler
   const double c = sizeof(cx<T>), re = sizeof(T);
   const double V = (double)br * nvec, G = (double)rows * nr, Gu = (double)s.rows() * nr;
   const double fft_flops = (double)rows * 5.0 * nr * std::log2((double)nr);
@@ -795,11 +800,23 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   }
   cx<T> *xr = w.xr.template as<cx<T>>();
   cx<T> *i1 = w.i1.template as<cx<T>>(), *i2 = w.i2.template as<cx<T>>();
+  const bool slab = sizeof(T) == 4 && s.slab;
   // pruned traffic: stick buffer (rows x nstick x n3) and plane buffer (rows x nplane x n2 x n3)
   const double S1 = (double)rows * s.nstick_max * s.fft[2];
   const double S2 = (double)rows * s.nplane_max * s.fft[1] * s.fft[2];
+  // FLOPs of the x-y line transforms of one pass on the slab path (planes + columns)
+  const double xy_flops = (double)rows * s.fft[2] *
+                          (s.nplane_max + s.fft[1]) * 5.0 * s.fft[0] * std::log2((double)s.fft[0]);
+  const double z_flops = (double)rows * s.nstick_max * 5.0 * s.fft[2] * std::log2((double)s.fft[2]);
   // 1. sphere -> real space (pruned Z, Y passes; full X pass)
-  {
+  if (slab) {
+    // sphere in, sticks out and back in, slabs out
+    ProfScope ps(pf, st, ST_FFT_INV, V * c + 2 * S1 * c + G * c, z_flops + xy_flops);
+    if constexpr (sizeof(T) == 4) {
+      sticks_inverse<T>(ctx, s, x, i1, nvec);
+      slab_inverse_yx(ctx, s, i1, xr, nvec);
+    }
+  } else {
     ProfScope ps(pf, st, ST_FFT_INV, V * c + 2 * S1 * c + 2 * S2 * c + G * c, fft_flops);
     pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);
   }
@@ -809,7 +826,16 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   cx<T> *hg = w.hgrid.template as<cx<T>>();
   const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
   if (use_h || use_xc) {
-    {
+    if (slab) {
+      // slabs and U (once per pass of up to 3 vectors) in, partials out and back, rho out
+      const double ng = slab_density_groups(s);
+      ProfScope ps(pf, st, ST_DENSITY,
+                   G * c + Gu * c * ((nvec + 2) / 3) + (2 * ng + 1) * 4 * nvec * nr * c,
+                   (double)nbs * nr * 40.0);
+      if constexpr (sizeof(T) == 4)
+        slab_density(ctx, s, xr, d.us.template as<float2>(), d.wk.template as<float>(),
+                     w.rhopart.template as<float2>(), rho, nvec);
+    } else {
       ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
                    (double)nbs * nr * 40.0);
       launch_density<T>(st, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
@@ -841,7 +867,21 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   // 5-6. local products fused into the forward X pass; pruned Y, Z passes with the
   //      sphere gather and + (kin - e) x fused into the last one
   cx<T> *h = w.h.template as<cx<T>>();
-  {
+  if (slab) {
+    // coefficients written and read back, slabs and U in, sticks out and back in,
+    // x read and h written on the sphere
+    ProfScope ps(pf, st, ST_FFT_FWD,
+                 4 * nvec * nr * (c + re) + 2 * nvec * nr * 48.0 + G * c + Gu * c + 2 * S1 * c +
+                     2 * V * c,
+                 xy_flops + z_flops + (double)nbs * nr * 64.0);
+    if constexpr (sizeof(T) == 4) {
+      slab_product_forward(ctx, s, xr, d.us.template as<float2>(), vp,
+                           d.vloc.template as<float>(), d.bfield.template as<float>(),
+                           w.coef.template as<float2>(), i1, nvec);
+      sticks_forward<T>(ctx, s, x, i1, d.kin.template as<T>(), d.evals.template as<T>(), h,
+                        nvec);
+    }
+  } else {
     ProfScope ps(pf, st, ST_FFT_FWD,
                  G * c + Gu * c + 4 * nvec * nr * (c + re) + 2 * S2 * c + 2 * S1 * c + 3 * V * c,
                  fft_flops + (double)nbs * nr * 64.0);
@@ -857,8 +897,16 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
                  2 * 8.0 * batch * (double)np_ * 2 * nb * npwx);
     cx<T> *proj = w.proj.template as<cx<T>>();
     cx<T> *dm = w.dmix.template as<cx<T>>();
-    gemm_tn<T>(ctx, w.part, d.beta.template as<cx<T>>(), npwx, (long long)np_ * npwx, nk, x, npwx,
-               bstride, proj, (long long)np_ * 2 * nb, 2 * nb, 1, np_, 2 * nb, npwx, batch);
+    bool tc = false;
+    if constexpr (sizeof(T) == 4)
+      if (s.tensor_gemm)
+        tc = tc_gemm_tn(ctx, w.part, d.beta.template as<float2>(), npwx, (long long)np_ * npwx,
+                        nk, x, npwx, bstride, proj, (long long)np_ * 2 * nb, 2 * nb, 1, np_,
+                        2 * nb, npwx, batch);
+    if (!tc)
+      gemm_tn<T>(ctx, w.part, d.beta.template as<cx<T>>(), npwx, (long long)np_ * npwx, nk, x,
+                 npwx, bstride, proj, (long long)np_ * 2 * nb, 2 * nb, 1, np_, 2 * nb, npwx,
+                 batch);
     long long tot = (long long)batch * nb * 2 * np_;
     dmix_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(proj, d.dnl.template as<cx<T>>(), dm,
                                                         np_, nb, batch);
@@ -874,8 +922,14 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
                  2 * 8.0 * batch * (double)nb * nb * 2 * npwx);
     cx<T> *ov = w.ovl.template as<cx<T>>();
     const cx<T> *ukq = d.ukq.template as<cx<T>>();
-    gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch1, h, 2LL * npwx, bstride, ov,
-               (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
+    bool tc = false;
+    if constexpr (sizeof(T) == 4)
+      if (s.tensor_gemm)
+        tc = tc_gemm_tn(ctx, w.part, ukq, 2LL * npwx, bstride, batch1, h, 2LL * npwx, bstride,
+                        ov, (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
+    if (!tc)
+      gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch1, h, 2LL * npwx, bstride, ov,
+                 (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
     gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h, y,
                2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk, batch1);
   }

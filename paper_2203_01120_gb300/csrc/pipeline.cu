@@ -22,12 +22,12 @@
 // Launch KERNEL<T, N>(args) for the register-line lengths; sets ok = false otherwise.
 #define TDLZ_REG_LAUNCH(n, KERNEL, grid, ...)                                          \
   switch (n) {                                                                       \
-    case 12: KERNEL<T, 12><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
-    case 16: KERNEL<T, 16><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
-    case 24: KERNEL<T, 24><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
-    case 36: KERNEL<T, 36><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
-    case 45: KERNEL<T, 45><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
-    case 48: KERNEL<T, 48><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__); break;        \
+    case 12: KERNEL<T, 12><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 12>()); break; \
+    case 16: KERNEL<T, 16><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 16>()); break; \
+    case 24: KERNEL<T, 24><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 24>()); break; \
+    case 36: KERNEL<T, 36><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 36>()); break; \
+    case 45: KERNEL<T, 45><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 45>()); break; \
+    case 48: KERNEL<T, 48><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 48>()); break; \
     default: ok = false;                                                             \
   }
 
@@ -137,7 +137,9 @@ __device__ __forceinline__ long long row_of_block() {
 
 // ---------------------------------------------------------------- inverse
 // Z pass: sticks of row `row`, tile of TL sticks; sphere coefficients gathered.
-template <class T, int TL>
+// TR = false writes the stick buffer as [row][stick][j3], TR = true as
+// [row][j3][stick] (the layout of the slab-fused stages).
+template <class T, int TL, bool TR = false>
 __global__ void __launch_bounds__(256)
     inv_z_kernel(const cx<T> *__restrict__ x, cx<T> *__restrict__ i1, const int *__restrict__ nst,
                  const int *__restrict__ smap, int nk, int nb, int npwx, int nsm, int n3, T scale,
@@ -164,10 +166,18 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   cx<T> *res = tile_fft<T, TL>(b0, b1, n3, st, tw, +1);
-  cx<T> *o = i1 + (row * nsm + s0) * n3;
-  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
-    int l = e / n3, j = e - l * n3;
-    if (l < nl) o[(long long)l * n3 + j] = res[j * P + l];
+  if (TR) {
+    cx<T> *o = i1 + row * n3 * (long long)nsm + s0;
+    for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+      int j = e / TL, l = e - j * TL;
+      if (l < nl) o[(long long)j * nsm + l] = res[j * P + l];
+    }
+  } else {
+    cx<T> *o = i1 + (row * nsm + s0) * n3;
+    for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+      int l = e / n3, j = e - l * n3;
+      if (l < nl) o[(long long)l * n3 + j] = res[j * P + l];
+    }
   }
 }
 
@@ -337,8 +347,8 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Z pass: sticks; writes sphere coefficients + (kin - e) x.
-template <class T, int TL>
+// Z pass: sticks; writes sphere coefficients + (kin - e) x.  TR as in inv_z_kernel.
+template <class T, int TL, bool TR = false>
 __global__ void __launch_bounds__(256)
     fwd_z_gather_kernel(const cx<T> *__restrict__ i1, const cx<T> *__restrict__ x,
                         cx<T> *__restrict__ h, const int *__restrict__ nst,
@@ -354,10 +364,18 @@ __global__ void __launch_bounds__(256)
   int nl = min(TL, nst[k] - s0);
   if (nl <= 0) return;
   cx<T> *b0 = reinterpret_cast<cx<T> *>(smem_raw), *b1 = b0 + n3 * P;
-  const cx<T> *src = i1 + (row * nsm + s0) * n3;
-  for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
-    int l = e / n3, j = e - l * n3;
-    b0[j * P + l] = l < nl ? src[(long long)l * n3 + j] : czero<T>();
+  if (TR) {
+    const cx<T> *src = i1 + row * n3 * (long long)nsm + s0;
+    for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+      int j = e / TL, l = e - j * TL;
+      b0[j * P + l] = l < nl ? src[(long long)j * nsm + l] : czero<T>();
+    }
+  } else {
+    const cx<T> *src = i1 + (row * nsm + s0) * n3;
+    for (int e = threadIdx.x; e < n3 * TL; e += blockDim.x) {
+      int l = e / n3, j = e - l * n3;
+      b0[j * P + l] = l < nl ? src[(long long)l * n3 + j] : czero<T>();
+    }
   }
   __syncthreads();
   cx<T> *res = tile_fft<T, TL>(b0, b1, n3, st, tw, -1);
@@ -387,7 +405,7 @@ template <class T, int N1>
 __global__ void __launch_bounds__(kRegThreads)
     inv_x_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ xr,
                      const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
-                     long long nr, long long rows, const cx<T> *__restrict__ tw) {
+                     long long nr, long long rows, const RegTw<T, N1> tw) {
   long long row = row_of_block();
   if (row >= rows) return;
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,7 +429,7 @@ template <class T, int N2>
 __global__ void __launch_bounds__(kRegThreads)
     inv_y_reg_kernel(const cx<T> *__restrict__ i1, cx<T> *__restrict__ i2,
                      const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
-                     int nsm, int npm, int n3, long long rows, const cx<T> *__restrict__ tw) {
+                     int nsm, int npm, int n3, long long rows, const RegTw<T, N2> tw) {
   long long row = row_of_block();
   if (row >= rows) return;
   int k = (int)((row / (2 * nb)) % nk);
@@ -430,63 +448,6 @@ __global__ void __launch_bounds__(kRegThreads)
   cx<T> *o = i2 + ((row * npm + p) * N2) * (long long)n3 + j3;
 #pragma unroll
   for (int j = 0; j < N2; ++j) o[(long long)j * n3] = a[j];
-}
-
-// Forward X pass with the products: thread per (band-side, column, spinor).
-template <class T, int N1>
-__global__ void __launch_bounds__(kRegThreads)
-    fwd_x_product_reg_kernel(const cx<T> *__restrict__ xr, const cx<T> *__restrict__ ur,
-                             const T *__restrict__ vloc, const T *__restrict__ bf,
-                             const cx<T> *__restrict__ v, cx<T> *__restrict__ i2,
-                             const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
-                             long long nr, long long nbs, int nvec,
-                             const cx<T> *__restrict__ tw) {
-  long long blk = row_of_block();
-  if (blk >= nbs) return;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long c = t >> 1;
-  const int sp = (int)(t & 1);
-  if (c >= n23) return;
-  // the vectors of one band-side are adjacent in the launch order, so the occupied
-  // orbitals they share are re-read from L2 rather than HBM
-  const long long nbs1 = 2LL * nk * nb;
-  const long long bs1 = blk / nvec, vec = blk - bs1 * nvec;
-  const long long bs = vec * nbs1 + bs1;
-  const int k = (int)((bs1 / nb) % nk);
-  const T s = (bs1 / ((long long)nk * nb)) == 0 ? T(1) : T(-1);
-  v += vec * 4 * nr;
-  ur += 2 * bs1 * nr;
-  const long long r0 = 2 * bs;
-  const cx<T> *x0p = xr + r0 * nr, *x1p = xr + (r0 + 1) * nr;
-  cx<T> a[N1];
-#pragma unroll
-  for (int j = 0; j < N1; ++j) {
-    long long r = (long long)j * n23 + c;
-    T vl = vloc[r], bx = bf[r], by = bf[nr + r], bz = bf[2 * nr + r];
-    cx<T> v0 = v[r], v1 = v[nr + r], v2 = v[2 * nr + r], v3 = v[3 * nr + r];
-    cx<T> x0 = x0p[r], x1 = x1p[r], u0 = ur[r], u1 = ur[nr + r];
-    cx<T> res;
-    if (sp == 0) {  // [vl + s bz] x0 + s(bx - i by) x1 + (v0 + s v3) u0 + s(v1 - i v2) u1
-      res = cscale<T>(x0, vl + s * bz);
-      cfma<T>(res, mk<T>(s * bx, -s * by), x1);
-      cfma<T>(res, mk<T>(v0.x + s * v3.x, v0.y + s * v3.y), u0);
-      cfma<T>(res, mk<T>(s * (v1.x + v2.y), s * (v1.y - v2.x)), u1);
-    } else {  // s(bx + i by) x0 + [vl - s bz] x1 + s(v1 + i v2) u0 + (v0 - s v3) u1
-      res = cscale<T>(x1, vl - s * bz);
-      cfma<T>(res, mk<T>(s * bx, s * by), x0);
-      cfma<T>(res, mk<T>(s * (v1.x - v2.y), s * (v1.y + v2.x)), u0);
-      cfma<T>(res, mk<T>(v0.x - s * v3.x, v0.y - s * v3.y), u1);
-    }
-    a[j] = res;
-  }
-  RegPlan<N1>::template run<T, -1>(a, tw);
-  const int *po = plof + (long long)k * N1;
-  cx<T> *o = i2 + (r0 + sp) * npm * n23 + c;
-#pragma unroll
-  for (int j = 0; j < N1; ++j) {
-    int p = __ldg(po + j);
-    if (p >= 0) o[(long long)p * n23] = a[j];
-  }
 }
 
 // Local products, elementwise and in place over x(r): one thread per (band-side,
@@ -530,7 +491,7 @@ template <class T, int N1>
 __global__ void __launch_bounds__(kRegThreads)
     fwd_x_reg_kernel(const cx<T> *__restrict__ xr, cx<T> *__restrict__ i2,
                      const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
-                     long long nr, long long rows, const cx<T> *__restrict__ tw) {
+                     long long nr, long long rows, const RegTw<T, N1> tw) {
   long long row = row_of_block();
   if (row >= rows) return;
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -554,7 +515,7 @@ template <class T, int N2>
 __global__ void __launch_bounds__(kRegThreads)
     fwd_y_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ i1,
                      const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
-                     int nsm, int npm, int n3, long long rows, const cx<T> *__restrict__ tw) {
+                     int nsm, int npm, int n3, long long rows, const RegTw<T, N2> tw) {
   long long row = row_of_block();
   if (row >= rows) return;
   int k = (int)((row / (2 * nb)) % nk);
@@ -686,7 +647,7 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
   if (ok) {
     dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n2, inv_y_reg_kernel, g, i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
-                    s.nb, nsm, npm, n3, rows, tw_of<T>(s.plan.ax[1]));
+                    s.nb, nsm, npm, n3, rows);
     TDLZ_LAUNCH_CHECK();
   }
   if (!ok) {
@@ -701,7 +662,7 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
   if (ok) {
     dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n1, inv_x_reg_kernel, g, i2, xr, s.pl_of.as<int>(), s.nk, s.nb, npm, n23, s.nr,
-                    rows, tw_of<T>(s.plan.ax[0]));
+                    rows);
     TDLZ_LAUNCH_CHECK();
   }
   if (!ok) {
@@ -732,7 +693,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
     TDLZ_LAUNCH_CHECK();
     dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n1, fwd_x_reg_kernel, g, xr, i2, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
-                    s.nr, rows, tw_of<T>(s.plan.ax[0]));
+                    s.nr, rows);
     TDLZ_LAUNCH_CHECK();
   }
   if (!ok) {
@@ -748,7 +709,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
   if (ok) {
     dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, g, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
-                    s.nb, nsm, npm, n3, rows, tw_of<T>(s.plan.ax[1]));
+                    s.nb, nsm, npm, n3, rows);
     TDLZ_LAUNCH_CHECK();
   }
   if (!ok) {
@@ -770,6 +731,40 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
   }
 }
 
+// Z passes alone, stick buffer in [row][j3][stick] order (slab-fused stages).
+template <class T>
+void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec) {
+  cudaStream_t st = ctx.stream;
+  const int n3 = s.fft[2];
+  const long long rows = s.rows() * nvec;
+  const int nsm = s.nstick_max;
+  size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
+  set_smem(inv_z_kernel<T, kTL, true>, sm);
+  inv_z_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+      x, i1t, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
+      (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  TDLZ_LAUNCH_CHECK();
+}
+
+template <class T>
+void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, const T *kin,
+                    const T *evals, cx<T> *h, int nvec) {
+  cudaStream_t st = ctx.stream;
+  const int n3 = s.fft[2];
+  const long long rows = s.rows() * nvec;
+  const int nsm = s.nstick_max;
+  TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * sizeof(cx<T>), st));
+  size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
+  set_smem(fwd_z_gather_kernel<T, kTL, true>, sm);
+  fwd_z_gather_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+      i1t, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm, n3,
+      (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  TDLZ_LAUNCH_CHECK();
+}
+
+template void sticks_inverse<float>(Context &, QSlot &, const float2 *, float2 *, int);
+template void sticks_forward<float>(Context &, QSlot &, const float2 *, const float2 *,
+                                    const float *, const float *, float2 *, int);
 template void pipeline_inverse<double>(Context &, QSlot &, const double2 *, double2 *, double2 *,
                                        double2 *, int);
 template void pipeline_inverse<float>(Context &, QSlot &, const float2 *, float2 *, float2 *,

@@ -22,4 +22,12 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
                       const T *vloc, const T *bf, const cx<T> *v, const T *kin, const T *evals,
                       cx<T> *i1, cx<T> *i2, cx<T> *h, int nvec);
 
+// Z passes alone, with the stick buffer i1t in [nvec*rows][n3][nstick_max] order
+// (slab-fused stages): sphere -> sticks, and sticks -> sphere + (kin - e) x.
+template <class T>
+void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec);
+template <class T>
+void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, const T *kin,
+                    const T *evals, cx<T> *h, int nvec);
+
 }  // namespace tdlz

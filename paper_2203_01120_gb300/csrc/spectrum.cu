@@ -161,6 +161,23 @@ __global__ void spectrum_kernel(SpecArgs a) {
     out[(long long)l * a.nomega] = make_double2(s * acc[l].x, s * acc[l].y);
 }
 
+// S(w) = -Im sum_ab P_ab chi_ba(w), chi[a][b][w] = chi_ba (chain a, row b)  (Eq. S_def)
+__global__ void structure_factor_kernel(const double2 *__restrict__ chi, int nomega, PerpProj p,
+                                        double *__restrict__ S) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nomega; w += gridDim.x * blockDim.x) {
+    double im = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) im += p.m[a][b] * chi[((long long)a * 3 + b) * nomega + w].y;
+    S[w] = -im;
+  }
+}
+
+void launch_structure_factor(cudaStream_t st, const double2 *chi, int nomega, const PerpProj &p,
+                             double *S) {
+  structure_factor_kernel<<<blocks_for(nomega, 128), 128, 0, st>>>(chi, nomega, p, S);
+  TDLZ_LAUNCH_CHECK();
+}
+
 void launch_spectrum(cudaStream_t st, const SpecArgs &a) {
   long long nthr = (long long)a.nchain * a.nomega;
   spectrum_kernel<<<blocks_for(nthr, 128), 128, 0, st>>>(a);

@@ -21,4 +21,12 @@ struct SpecArgs {
 
 void launch_spectrum(cudaStream_t st, const SpecArgs &a);
 
+// P_perp(q) = 1 - q q^T / q^2
+struct PerpProj {
+  double m[3][3];
+};
+// S[w] = -Im Tr[P chi(w)] from the 3 x 3 susceptibility chi[mu][lambda][w] (device arrays).
+void launch_structure_factor(cudaStream_t st, const double2 *chi, int nomega, const PerpProj &p,
+                             double *S);
+
 }  // namespace tdlz

@@ -1,0 +1,335 @@
+// Reduction GEMMs of the mixed-precision Liouvillian on the 5th-generation tensor
+// cores (tcgen05, TF32 operands in shared memory, FP32 accumulators in TMEM).
+//
+//   C[b][m][n] = sum_k conj(A[b % amod][m][k]) B[b][n][k]        (complex)
+//
+// used for the Kleinman-Bylander projections <beta|x> (V_NL in Eq. H0_k_plus_q)
+// and the occupied-state overlaps <U_kq|h> of P_c (Eqs. P_minus_q2, P_plus_q2).
+//
+// Complex -> real: with interleaved (re, im) rows, Re C = A_int . B_int and
+// Im C = A_rot . B_int where A_rot = (-a.y, a.x) per element, so one real GEMM
+// with the 2M rows [A_int; A_rot] against the rows of B gives both parts
+// (2M <= 128 = the MMA's M).  The batches that share one A (b = a + j amod) are
+// stacked as the N rows of one tile (N <= 256).
+//
+// 3xTF32: every FP32 operand x is split into hi = tf32(x) and lo = tf32(x - hi)
+// while it is staged into shared memory, and D += Ahi Bhi + Ahi Blo + Alo Bhi
+// keeps FP32-level accuracy (the dropped lo*lo term is ~2^-22 relative).
+//
+// Shared-memory operands use the canonical K-major layout without swizzle: core
+// matrices of 8 rows x 16 bytes; the leading byte offset steps between 16-byte
+// K chunks, the stride byte offset between 8-row groups.  One CTA per
+// (A batch, N tile, K split); a two-stage pipeline overlaps the staging of K tile
+// t+1 (global loads, TF32 split) with the MMAs of tile t; the partial sums go to
+// a split-K buffer that a second kernel reduces in fixed order.
+#include <cstdint>
+
+#include "engine.cuh"
+#include "tc_gemm.cuh"
+
+namespace tdlz {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kKT = 32;                      // K tile: 32 reals (16 complex) = 128 bytes per row
+constexpr int kChunks = kKT / 4;             // 16-byte chunks per row in a K tile
+constexpr uint32_t kATile = 128 * kKT * 4;   // bytes of one A tile (hi or lo)
+constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
+
+__device__ int g_tc_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// K-major, no swizzle: start address, leading (K chunk) and stride (8-row group) offsets.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void split4(float4 v, float4 &hi, float4 &lo) {
+  hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+  lo = make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z),
+                   tf32_rna(v.w - hi.w));
+}
+
+// byte offset of (row r, 16-byte chunk c) in a canonical tile whose chunks are `lbo` apart
+__device__ __forceinline__ uint32_t tile_off(int r, int c, uint32_t lbo) {
+  return (uint32_t)c * lbo + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+struct TcArgs {
+  const float2 *A;
+  long long lda, sA;
+  int amod;
+  const float2 *B;
+  long long ldb, sB;
+  int M, N;        // complex output rows (A rows) and columns per batch (B rows)
+  long long K;     // complex contraction length
+  int nj;          // batches per A (batch / amod)
+  int ntot, nt;    // stacked B rows (nj * N) and rows per N tile (multiple of 16)
+  int ntiles, nsplit, kt_per_split, nkt;
+  uint32_t tmem_cols;
+  float *part;     // [nsplit][amod][ntiles][128][nt]
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nt = g.nt;
+  const uint32_t lboA = 16 * 128, lboB = (uint32_t)(nt / 8) * 128;
+  const uint32_t bTile = (uint32_t)nt * kKT * 4;
+  const uint32_t stage_bytes = 2 * kATile + 2 * bTile;
+  // CTA coordinates: x = N tile, y = A batch, z = K split
+  const int tile = blockIdx.x, a = blockIdx.y, z = blockIdx.z;
+  const int kt0 = z * g.kt_per_split;
+  const int kt1 = min(g.nkt, kt0 + g.kt_per_split);
+  const int nloc = kt1 - kt0;
+
+  // zero both stages once (rows >= 2M of A and rows >= ntot of B stay zero)
+  for (uint32_t i = tid; i < 2 * stage_bytes / 16; i += blockDim.x)
+    reinterpret_cast<float4 *>(tc_smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(g.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = (1u << 4)                           // D: F32
+                         | (2u << 7) | (2u << 10)             // A, B: TF32
+                         | ((uint32_t)(nt >> 3) << 17)        // N >> 3
+                         | ((uint32_t)(128 >> 4) << 24);      // M >> 4
+  const float2 *Ab = g.A + (long long)a * g.sA;
+  const int sub = tid & (kChunks - 1), rstep = kTcThreads / kChunks;
+
+  for (int it = 0; it < nloc; ++it) {
+    const int s = it & 1;
+    if (it >= 2) {
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    unsigned char *st = tc_smem + (size_t)s * stage_bytes;
+    unsigned char *Ahi = st, *Alo = st + kATile, *Bhi = st + 2 * kATile, *Blo = Bhi + bTile;
+    const long long kc0 = (long long)(kt0 + it) * (kKT / 2);  // first complex index of the tile
+    const long long kc = kc0 + 2 * sub;                        // this thread's complex pair
+    // A rows: [A_int; A_rot]
+    for (int m = tid / kChunks; m < g.M; m += rstep) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2 *row = Ab + (long long)m * g.lda;
+      if (kc < g.K) {
+        const float2 t0 = __ldg(row + kc);
+        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
+        v = make_float4(t0.x, t0.y, t1.x, t1.y);
+      }
+      float4 hi, lo;
+      split4(v, hi, lo);
+      *reinterpret_cast<float4 *>(Ahi + tile_off(m, sub, lboA)) = hi;
+      *reinterpret_cast<float4 *>(Alo + tile_off(m, sub, lboA)) = lo;
+      split4(make_float4(-v.y, v.x, -v.w, v.z), hi, lo);
+      *reinterpret_cast<float4 *>(Ahi + tile_off(g.M + m, sub, lboA)) = hi;
+      *reinterpret_cast<float4 *>(Alo + tile_off(g.M + m, sub, lboA)) = lo;
+    }
+    // B rows of this N tile: stacked (j, n) -> batch a + j amod, row n
+    for (int r = tid / kChunks; r < nt; r += rstep) {
+      const int R = tile * nt + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (R < g.ntot) {
+        const int j = R / g.N, n = R - j * g.N;
+        const float2 *row = g.B + (long long)(a + (long long)j * g.amod) * g.sB + (long long)n * g.ldb;
+        if (kc < g.K) {
+          const float2 t0 = row[kc];
+          const float2 t1 = kc + 1 < g.K ? row[kc + 1] : make_float2(0.f, 0.f);
+          v = make_float4(t0.x, t0.y, t1.x, t1.y);
+        }
+      }
+      float4 hi, lo;
+      split4(v, hi, lo);
+      *reinterpret_cast<float4 *>(Bhi + tile_off(r, sub, lboB)) = hi;
+      *reinterpret_cast<float4 *>(Blo + tile_off(r, sub, lboB)) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi),
+                     bl = smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < kKT / 8; ++ks) {
+        const uint32_t oa = 2 * ks * lboA, ob = 2 * ks * lboB;
+        const uint64_t dah = smem_desc(ah + oa, lboA, 128), dal = smem_desc(al + oa, lboA, 128);
+        const uint64_t dbh = smem_desc(bh + ob, lboB, 128), dbl = smem_desc(bl + ob, lboB, 128);
+        const uint32_t acc0 = (it > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.eq.u32 p, 1, 1;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %4, %5, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbl), "r"(idesc), "l"(dal), "l"(dbh));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar[s])));
+    }
+  }
+  // drain: the last commit covers every MMA issued before it
+  if (nloc > 0 && !abort_flag) {
+    const int last = nloc - 1;
+    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_flag = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = !abort_flag && nloc > 0;
+  if (!ok && tid == 0 && abort_flag) atomicExch(&g_tc_timeout, 1);
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+  const int row = 32 * warp + (tid & 31);
+  float *out = g.part + ((((long long)z * gridDim.y + a) * g.ntiles + tile) * 128 + row) * nt;
+  for (int c0 = 0; c0 < nt; c0 += 8) {
+    uint32_t r[8];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (row < 2 * g.M) {
+      float4 *o = reinterpret_cast<float4 *>(out + c0);
+      if (ok) {
+        o[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
+                           __uint_as_float(r[3]));
+        o[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]),
+                           __uint_as_float(r[7]));
+      } else {
+        o[0] = o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(g.tmem_cols));
+}
+
+// C[b*sC + m*ldcm + n*ldcn] = sum_z (part[z][a][t][m][col], part[z][a][t][M+m][col])
+// with b = a + j amod and stacked row R = j N + n = t nt + col.
+__global__ void tc_reduce_kernel(const float *__restrict__ part, float2 *__restrict__ C, int M,
+                                 int N, int amod, int nj, int ntiles, int nt, int nsplit,
+                                 long long sC, long long ldcm, long long ldcn) {
+  const long long total = (long long)amod * nj * M * N;
+  const long long zstride = (long long)amod * ntiles * 128 * nt;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / ((long long)M * N);
+    const int rem = (int)(e - b * M * N);
+    const int m = rem / N, n = rem - m * N;
+    const int a = (int)(b % amod), j = (int)(b / amod);
+    const int R = j * N + n, t = R / nt, col = R - t * nt;
+    const float *p = part + (((long long)a * ntiles + t) * 128) * nt + col;
+    float re = 0.f, im = 0.f;
+    for (int zz = 0; zz < nsplit; ++zz) {
+      re += p[(long long)zz * zstride + (long long)m * nt];
+      im += p[(long long)zz * zstride + (long long)(M + m) * nt];
+    }
+    C[b * sC + m * ldcm + n * ldcn] = make_float2(re, im);
+  }
+}
+
+}  // namespace
+
+bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
+                int amod, const float2 *B, long long ldb, long long sB, float2 *C, long long sC,
+                long long ldcm, long long ldcn, int M, int N, long long K, int batch) {
+  if (2 * M > 128 || M < 1 || N < 1 || K < 1 || amod < 1 || batch % amod != 0) return false;
+  TcArgs g;
+  g.A = A;
+  g.lda = lda;
+  g.sA = sA;
+  g.amod = amod;
+  g.B = B;
+  g.ldb = ldb;
+  g.sB = sB;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.nj = batch / amod;
+  g.ntot = g.nj * N;
+  g.ntiles = (g.ntot + 255) / 256;
+  g.nt = ((g.ntot + g.ntiles - 1) / g.ntiles + 15) / 16 * 16;
+  g.nkt = (int)((K + kKT / 2 - 1) / (kKT / 2));
+  const int ctas = amod * g.ntiles;
+  int ns = std::max(1, std::min(g.nkt, (2 * 152 + ctas - 1) / ctas));
+  g.kt_per_split = (g.nkt + ns - 1) / ns;
+  g.nsplit = (g.nkt + g.kt_per_split - 1) / g.kt_per_split;
+  g.tmem_cols = 32;
+  while (g.tmem_cols < (uint32_t)g.nt) g.tmem_cols *= 2;
+  const size_t need = (size_t)g.nsplit * amod * g.ntiles * 128 * g.nt * sizeof(float);
+  if (need > partbuf.bytes) return false;
+  g.part = partbuf.as<float>();
+  const size_t smem = 2 * (2 * (size_t)kATile + 2 * (size_t)g.nt * kKT * 4);
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_tn_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.ntiles, amod, g.nsplit);
+  tc_gemm_tn_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(g);
+  TDLZ_LAUNCH_CHECK();
+  const long long total = (long long)batch * M * N;
+  tc_reduce_kernel<<<blocks_for(total), 256, 0, ctx.stream>>>(g.part, C, M, N, amod, g.nj,
+                                                               g.ntiles, g.nt, g.nsplit, sC,
+                                                               ldcm, ldcn);
+  TDLZ_LAUNCH_CHECK();
+  return true;
+}
+
+void tc_gemm_check() {
+  int flag = 0;
+  TDLZ_CUDA_TRY(cudaMemcpyFromSymbol(&flag, g_tc_timeout, sizeof(int)));
+  if (flag) {
+    int zero = 0;
+    TDLZ_CUDA_TRY(cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int)));
+    throw Error{TDLZ_ERR_TIMEOUT, "tensor-core GEMM: an mbarrier wait ran out (results invalid)"};
+  }
+}
+
+}  // namespace tdlz

@@ -292,3 +292,26 @@ def test_extrapolation_terminator_equals_extended_system(c0_chains, kind):
         assert np.allclose(ext.beta[60::2], ext.beta[60]) and np.allclose(ext.beta[61::2], ext.beta[61])
     trunc = chi_extrapolated(c, OMEGAS, eta, w, 60, 400, "no")
     assert np.allclose(trunc, chi_banded(c, OMEGAS, eta, w, m=60), rtol=1e-12, atol=0)
+
+
+def test_structure_factor_projector_pins():
+    """S(q, w) = -Im Tr[P_perp chi]: for q along x it keeps chi_yy + chi_zz; it is
+    invariant under a common rotation of q and chi (R chi R^T); the longitudinal
+    part q^ chi q^ drops out (chi = q q^T c gives S = 0)."""
+    from oracle.spectrum import structure_factor
+    rng = np.random.default_rng(3)
+    chi_lm = rng.normal(size=(3, 3, 7)) + 1j * rng.normal(size=(3, 3, 7))  # [lambda][mu][w]
+    chi3 = np.transpose(chi_lm, (1, 0, 2))  # [mu][lambda][w]
+    s = structure_factor(chi3, [2.0, 0.0, 0.0])
+    assert np.allclose(s, -(chi_lm[1, 1] + chi_lm[2, 2]).imag, rtol=0, atol=1e-14)
+    th = 0.7
+    rot = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    rot = rot @ np.array([[1, 0, 0], [0, np.cos(0.3), -np.sin(0.3)], [0, np.sin(0.3), np.cos(0.3)]])
+    q = np.array([0.3, -1.1, 0.4])
+    chi_rot = np.einsum("ab,bcw,dc->adw", rot, chi_lm, rot)
+    s1 = structure_factor(np.transpose(chi_lm, (1, 0, 2)), q)
+    s2 = structure_factor(np.transpose(chi_rot, (1, 0, 2)), rot @ q)
+    assert np.allclose(s1, s2, rtol=0, atol=1e-13)
+    qh = q / np.linalg.norm(q)
+    long_only = np.einsum("a,b,w->abw", qh, qh, chi_lm[0, 0])
+    assert np.allclose(structure_factor(np.transpose(long_only, (1, 0, 2)), q), 0, atol=1e-14)
