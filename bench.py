@@ -54,6 +54,8 @@ def parse():
                     help="chi columns per GPU (x, y, z), advanced together")
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="profiling runs: time the mixed chains only (no FP64 chains, no chi error)")
     ap.add_argument("--bundle", default=None, help="cache file for the generated ground state")
     ap.add_argument("--profile-apply", type=int, default=0,
                     help="run N Liouvillian applications on a shape-only bundle (for profilers)")
@@ -309,16 +311,19 @@ def run_tdlz(args):
     _, _, _, prof, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_MIXED, 1, args.steps,
                                          stream, profile=True)
     fp64_steps = max(3, args.steps // 4)
-    sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_FP64, 1,
-                                                          fp64_steps, stream, profile=True)
-    # ------------------------------------------------------------ chi error mixed vs FP64
     m = args.chi_steps
-    r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)
-    r32 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
-    c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1)
-    c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)
-    chi_err = max(float(np.linalg.norm(c32[i] - c64[i]) / np.linalg.norm(c64[i][mu]))
-                  for i, mu in enumerate(mus))
+    if args.mixed_only:  # profiling runs: the mixed chains above are the whole workload
+        sps_fp64, wall_fp64, prof64, chi_err = None, None, {}, None
+    else:
+        sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(
+            ctx, q, mus, args.flavor, TDLZ_FP64, 1, fp64_steps, stream, profile=True)
+        # ------------------------------------------------------------ chi error mixed vs FP64
+        r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)
+        r32 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
+        c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1)
+        c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)
+        chi_err = max(float(np.linalg.norm(c32[i] - c64[i]) / np.linalg.norm(c64[i][mu]))
+                      for i, mu in enumerate(mus))
     ctx.close()
     if rank != 0:
         return
@@ -353,8 +358,9 @@ def run_tdlz(args):
                    "chains_per_gpu": len(mus), "parallelism": f"replicas{world}",
                    "ms_per_step_is": "one step of every chain of the GPU (advanced together)",
                    "l2": "inputs larger than L2 (per-step working set > 5 GB)"},
-        "fp64": {"value": sps_fp64, "unit": "steps/s", "steps": fp64_steps,
-                 "ms_per_step": 1000 * wall_fp64 / fp64_steps},
+        "fp64": None if sps_fp64 is None else {
+            "value": sps_fp64, "unit": "steps/s", "steps": fp64_steps,
+            "ms_per_step": 1000 * wall_fp64 / fp64_steps},
         "chi_rel_err": chi_err, "chi_steps": m, "chi_tolerance": 1e-4,
         "roofline": {"bound": "hbm", "stage": top, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "traffic": None,

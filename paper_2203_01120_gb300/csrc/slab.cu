@@ -38,6 +38,7 @@ struct SlabTables {
 __device__ __forceinline__ float2 f2zero() { return make_float2(0.f, 0.f); }
 
 __host__ __device__ constexpr int line_threads(int n) { return ((2 * n + 31) / 32) * 32; }
+constexpr int kSlabFwdThreads = 128;
 __host__ __device__ inline int even(int n) { return (n + 1) & ~1; }
 
 // Inverse Y then X transforms of a row pair (the two spinor rows of a band-side)
@@ -102,22 +103,24 @@ __global__ void __launch_bounds__(line_threads(N))
 }
 
 // Products and forward X, Y transforms of one band-side (both spinor rows) on
-// plane j3, sticks written to i1t.  The X-phase thread (spin sp, column j2) forms
-//   t_sp(j1) = a_sp0 x0 + a_sp1 x1 + c_sp0 u0 + c_sp1 u1   at (j1, j2)
-// from xr, the U slab and the plane's product coefficients, transforms the line
-// and keeps the sphere's planes; the Y phase keeps the sphere's sticks.
+// plane j3, sticks written to i1t.  All threads first form
+//   t0 = a00 x0 + a01 x1 + c00 u0 + c01 u1,  t1 = a10 x0 + a11 x1 + c10 u0 + c11 u1
+// pointwise over the plane (coalesced loads of xr, the U slab and the coefficient
+// planes) into shared memory; then thread (spin sp, column j2) transforms its X
+// line and keeps the sphere's planes, and the Y lines keep the sphere's sticks.
 template <int N>
-__global__ void __launch_bounds__(line_threads(N))
+__global__ void __launch_bounds__(kSlabFwdThreads)
     slab_product_fwd_kernel(const float2 *__restrict__ xr, const float2 *__restrict__ us,
                             const float2 *__restrict__ coef, float2 *__restrict__ i1t,
                             SlabTables tb, int nvec, const RegTw<float, N> tw) {
   extern __shared__ float4 slab_smem_raw[];
   constexpr int YP = N + 1, NN = N * N;
   const int sst = even(tb.nsm);
-  float2 *S = reinterpret_cast<float2 *>(slab_smem_raw);  // [2][nsm]
-  float2 *Y = S + 2 * sst;                                 // [2][npm][N+1]
-  int *sid = reinterpret_cast<int *>(Y + 2 * tb.npm * YP); // [npm][N]
-  int *pof = sid + tb.npm * N;                             // [N]
+  float2 *X = reinterpret_cast<float2 *>(slab_smem_raw);   // [2][NN]
+  float2 *S = X + 2 * NN;                                   // [2][nsm]
+  float2 *Y = S + 2 * sst;                                  // [2][npm][N+1]
+  int *sid = reinterpret_cast<int *>(Y + 2 * tb.npm * YP);  // [npm][N]
+  int *pof = sid + tb.npm * N;                              // [N]
   const long long nbs1 = 2LL * tb.nk * tb.nb;
   // the vectors of one band-side are neighbouring CTAs: they share the U slab in L2
   const long long blk = blockIdx.x + (long long)gridDim.x * blockIdx.z;
@@ -132,34 +135,38 @@ __global__ void __launch_bounds__(line_threads(N))
   for (int e = threadIdx.x; e < npl * N; e += blockDim.x)
     sid[e] = __ldg(tb.st_id + (long long)k * tb.npm * N + e);
   for (int e = threadIdx.x; e < N; e += blockDim.x) pof[e] = __ldg(tb.pl_of + (long long)k * N + e);
-  __syncthreads();
-  if (threadIdx.x < 2 * N) {
-    const int sp = threadIdx.x / N, j2 = threadIdx.x - sp * N;
-    const long long nr = (long long)tb.n3 * NN, o = (long long)j3 * NN + j2;
+  {
+    const long long nr = (long long)tb.n3 * NN, o = (long long)j3 * NN;
     const float2 *x0p = xr + row0 * nr + o, *x1p = x0p + nr;
     const float2 *u0p = us + (bs1 * 2) * nr + o, *u1p = u0p + nr;
     // coefficient planes of this vector and side: (a00, a11), a01, c00, c01, c10, c11
     const float2 *cp = coef + ((long long)vec * 2 + side) * 6 * nr + o;
-    const float2 *caa = cp, *c01 = cp + nr, *cu0 = cp + (2 + 2 * sp) * nr, *cu1 = cu0 + nr;
+#pragma unroll 2
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+      const float2 x0 = x0p[i], x1 = x1p[i];
+      const float2 u0 = __ldg(u0p + i), u1 = __ldg(u1p + i);
+      const float2 d = __ldg(cp + i), f = __ldg(cp + nr + i);
+      const float2 c00 = __ldg(cp + 2 * nr + i), c01 = __ldg(cp + 3 * nr + i);
+      const float2 c10 = __ldg(cp + 4 * nr + i), c11 = __ldg(cp + 5 * nr + i);
+      float2 t0 = make_float2(d.x * x0.x, d.x * x0.y);
+      cfma<float>(t0, f, x1);
+      cfma<float>(t0, c00, u0);
+      cfma<float>(t0, c01, u1);
+      float2 t1 = make_float2(d.y * x1.x, d.y * x1.y);
+      cfma<float>(t1, make_float2(f.x, -f.y), x0);
+      cfma<float>(t1, c10, u0);
+      cfma<float>(t1, c11, u1);
+      X[i] = t0;
+      X[NN + i] = t1;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int sp = t / N, j2 = t - sp * N;
+    const float2 *src = X + sp * NN + j2;
     float2 a[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const float2 x0 = x0p[j * N], x1 = x1p[j * N];
-      const float2 u0 = __ldg(u0p + j * N), u1 = __ldg(u1p + j * N);
-      const float2 d = __ldg(caa + j * N), f = __ldg(c01 + j * N);
-      const float2 g0 = __ldg(cu0 + j * N), g1 = __ldg(cu1 + j * N);
-      float2 t2;
-      if (sp == 0) {  // a00 x0 + a01 x1 + c00 u0 + c01 u1
-        t2 = make_float2(d.x * x0.x, d.x * x0.y);
-        cfma<float>(t2, f, x1);
-      } else {  // a11 x1 + a10 x0 + c10 u0 + c11 u1 (a10 = conj(a01))
-        t2 = make_float2(d.y * x1.x, d.y * x1.y);
-        cfma<float>(t2, make_float2(f.x, -f.y), x0);
-      }
-      cfma<float>(t2, g0, u0);
-      cfma<float>(t2, g1, u1);
-      a[j] = t2;
-    }
+    for (int j = 0; j < N; ++j) a[j] = src[j * N];
     RegPlan<N>::template run<float, -1>(a, tw);
     float2 *out = Y + sp * tb.npm * YP + j2;
 #pragma unroll
@@ -326,6 +333,10 @@ size_t smem_pair(const QSlot &s) {
              sizeof(float2) +
          ((size_t)s.nplane_max + 1) * s.fft[0] * sizeof(int);
 }
+// the product + forward kernel also holds both spinor planes of products
+size_t smem_forward(const QSlot &s) {
+  return smem_pair(s) + 2 * (size_t)s.fft[0] * s.fft[1] * sizeof(float2);
+}
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -361,7 +372,7 @@ dim3 plane_grid(long long count, int n3) {
 bool slab_supported(const QSlot &s) {
   const int n = s.fft[0];
   if (s.fft[1] != n || !reg_fft_length(n)) return false;
-  return smem_pair(s) <= kSmemLimit;
+  return smem_forward(s) <= kSmemLimit;
 }
 
 void slab_build_u(Context &ctx, QSlot &s, const double2 *ur, DevBuf &us) {
@@ -425,11 +436,11 @@ void slab_product_forward(Context &ctx, QSlot &s, const float2 *xr, const float2
   slab_coef_kernel<<<blocks_for(total), 256, 0, ctx.stream>>>(vpot, vloc, bf, coef, nn,
                                                               s.fft[2], s.nr, total);
   TDLZ_LAUNCH_CHECK();
-  const size_t sm = smem_pair(s);
+  const size_t sm = smem_forward(s);
   const dim3 grid = plane_grid((long long)nvec * 2 * s.nk * s.nb, s.fft[2]);
 #define TDLZ_SLAB_FWD(NV)                                                               \
   set_smem_attr(slab_product_fwd_kernel<NV>, sm);                                       \
-  slab_product_fwd_kernel<NV><<<grid, line_threads(NV), sm, ctx.stream>>>(xr, us, coef, i1t, \
+  slab_product_fwd_kernel<NV><<<grid, kSlabFwdThreads, sm, ctx.stream>>>(xr, us, coef, i1t,  \
                                                                           tb, nvec,     \
                                                                           regtw<float, NV>());
   TDLZ_SLAB_SWITCH(s.fft[0], TDLZ_SLAB_FWD)

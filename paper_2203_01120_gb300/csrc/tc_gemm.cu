@@ -36,6 +36,9 @@ constexpr int kKT = 32;                      // K tile: 32 reals (16 complex) = 
 constexpr int kChunks = kKT / 4;             // 16-byte chunks per row in a K tile
 constexpr uint32_t kATile = 128 * kKT * 4;   // bytes of one A tile (hi or lo)
 constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
+constexpr int kRowStep = kTcThreads / kChunks;  // rows staged per pass (16)
+constexpr int kMaxA = 64 / kRowStep;            // A rows per thread (M <= 64)
+constexpr int kMaxB = 256 / kRowStep;           // B rows per thread (N tile <= 256)
 
 __device__ int g_tc_timeout = 0;
 
@@ -138,10 +141,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
                          | ((uint32_t)(nt >> 3) << 17)        // N >> 3
                          | ((uint32_t)(128 >> 4) << 24);      // M >> 4
   const float2 *Ab = g.A + (long long)a * g.sA;
-  const int sub = tid & (kChunks - 1), rstep = kTcThreads / kChunks;
+  const int sub = tid & (kChunks - 1), rstep = kRowStep;
 
   for (int it = 0; it < nloc; ++it) {
     const int s = it & 1;
+    const long long kc0 = (long long)(kt0 + it) * (kKT / 2);  // first complex index of the tile
+    const long long kc = kc0 + 2 * sub;                        // this thread's complex pair
+    // issue every global load of the tile first (read-only path), then split and store:
+    // loads interleaved with shared-memory stores would otherwise serialise
+    float4 va[kMaxA], vb[kMaxB];
+#pragma unroll
+    for (int i = 0; i < kMaxA; ++i) {
+      const int m = tid / kChunks + i * rstep;
+      va[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < g.M && kc < g.K) {
+        const float2 *row = Ab + (long long)m * g.lda;
+        const float2 t0 = __ldg(row + kc);
+        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
+        va[i] = make_float4(t0.x, t0.y, t1.x, t1.y);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxB; ++i) {
+      const int r = tid / kChunks + i * rstep;
+      const int R = tile * nt + r;
+      vb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < nt && R < g.ntot && kc < g.K) {
+        const int j = R / g.N, n = R - j * g.N;
+        const float2 *row =
+            g.B + (long long)(a + (long long)j * g.amod) * g.sB + (long long)n * g.ldb;
+        const float2 t0 = __ldg(row + kc);
+        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
+        vb[i] = make_float4(t0.x, t0.y, t1.x, t1.y);
+      }
+    }
+    // the loads above are in flight while the MMAs of tile it-2 release stage s
     if (it >= 2) {
       if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
     }
@@ -149,42 +183,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
     if (abort_flag) break;
     unsigned char *st = tc_smem + (size_t)s * stage_bytes;
     unsigned char *Ahi = st, *Alo = st + kATile, *Bhi = st + 2 * kATile, *Blo = Bhi + bTile;
-    const long long kc0 = (long long)(kt0 + it) * (kKT / 2);  // first complex index of the tile
-    const long long kc = kc0 + 2 * sub;                        // this thread's complex pair
-    // A rows: [A_int; A_rot]
-    for (int m = tid / kChunks; m < g.M; m += rstep) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float2 *row = Ab + (long long)m * g.lda;
-      if (kc < g.K) {
-        const float2 t0 = __ldg(row + kc);
-        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
-        v = make_float4(t0.x, t0.y, t1.x, t1.y);
+    // A rows [A_int; A_rot]
+#pragma unroll
+    for (int i = 0; i < kMaxA; ++i) {
+      const int m = tid / kChunks + i * rstep;
+      if (m < g.M) {
+        float4 hi, lo;
+        split4(va[i], hi, lo);
+        *reinterpret_cast<float4 *>(Ahi + tile_off(m, sub, lboA)) = hi;
+        *reinterpret_cast<float4 *>(Alo + tile_off(m, sub, lboA)) = lo;
+        split4(make_float4(-va[i].y, va[i].x, -va[i].w, va[i].z), hi, lo);
+        *reinterpret_cast<float4 *>(Ahi + tile_off(g.M + m, sub, lboA)) = hi;
+        *reinterpret_cast<float4 *>(Alo + tile_off(g.M + m, sub, lboA)) = lo;
       }
-      float4 hi, lo;
-      split4(v, hi, lo);
-      *reinterpret_cast<float4 *>(Ahi + tile_off(m, sub, lboA)) = hi;
-      *reinterpret_cast<float4 *>(Alo + tile_off(m, sub, lboA)) = lo;
-      split4(make_float4(-v.y, v.x, -v.w, v.z), hi, lo);
-      *reinterpret_cast<float4 *>(Ahi + tile_off(g.M + m, sub, lboA)) = hi;
-      *reinterpret_cast<float4 *>(Alo + tile_off(g.M + m, sub, lboA)) = lo;
     }
     // B rows of this N tile: stacked (j, n) -> batch a + j amod, row n
-    for (int r = tid / kChunks; r < nt; r += rstep) {
-      const int R = tile * nt + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (R < g.ntot) {
-        const int j = R / g.N, n = R - j * g.N;
-        const float2 *row = g.B + (long long)(a + (long long)j * g.amod) * g.sB + (long long)n * g.ldb;
-        if (kc < g.K) {
-          const float2 t0 = row[kc];
-          const float2 t1 = kc + 1 < g.K ? row[kc + 1] : make_float2(0.f, 0.f);
-          v = make_float4(t0.x, t0.y, t1.x, t1.y);
-        }
+#pragma unroll
+    for (int i = 0; i < kMaxB; ++i) {
+      const int r = tid / kChunks + i * rstep;
+      if (r < nt) {
+        float4 hi, lo;
+        split4(vb[i], hi, lo);
+        *reinterpret_cast<float4 *>(Bhi + tile_off(r, sub, lboB)) = hi;
+        *reinterpret_cast<float4 *>(Blo + tile_off(r, sub, lboB)) = lo;
       }
-      float4 hi, lo;
-      split4(v, hi, lo);
-      *reinterpret_cast<float4 *>(Bhi + tile_off(r, sub, lboB)) = hi;
-      *reinterpret_cast<float4 *>(Blo + tile_off(r, sub, lboB)) = lo;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -300,13 +322,16 @@ bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, l
   g.nt = ((g.ntot + g.ntiles - 1) / g.ntiles + 15) / 16 * 16;
   g.nkt = (int)((K + kKT / 2 - 1) / (kKT / 2));
   const int ctas = amod * g.ntiles;
-  int ns = std::max(1, std::min(g.nkt, (2 * 152 + ctas - 1) / ctas));
-  g.kt_per_split = (g.nkt + ns - 1) / ns;
+  // about two waves of one-CTA-per-SM work, within the split-K scratch
+  const size_t per_split = (size_t)amod * g.ntiles * 128 * g.nt * sizeof(float);
+  const long long fit = (long long)(partbuf.bytes / per_split);
+  if (fit < 1) return false;
+  long long ns = std::max(1, std::min(g.nkt, (2 * 152 + ctas - 1) / ctas));
+  ns = std::min(ns, fit);
+  g.kt_per_split = (int)((g.nkt + ns - 1) / ns);
   g.nsplit = (g.nkt + g.kt_per_split - 1) / g.kt_per_split;
   g.tmem_cols = 32;
   while (g.tmem_cols < (uint32_t)g.nt) g.tmem_cols *= 2;
-  const size_t need = (size_t)g.nsplit * amod * g.ntiles * 128 * g.nt * sizeof(float);
-  if (need > partbuf.bytes) return false;
   g.part = partbuf.as<float>();
   const size_t smem = 2 * (2 * (size_t)kATile + 2 * (size_t)g.nt * kKT * 4);
   TDLZ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_tn_kernel,

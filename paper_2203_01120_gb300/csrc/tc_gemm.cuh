@@ -8,7 +8,7 @@ namespace tdlz {
 // C[b*sC + m*ldcm + n*ldcn] = sum_k conj(A[(b % amod)*sA + m*lda + k]) B[b*sB + n*ldb + k]
 // for b < batch (complex FP32, FP32 accumulation).  Returns false, launching nothing,
 // for shapes outside the kernel (2M > 128, batch not a multiple of amod, or partbuf
-// too small); the caller then uses the CUDA-core GEMM.
+// smaller than one split); the caller then uses the CUDA-core GEMM.
 bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
                 int amod, const float2 *B, long long ldb, long long sB, float2 *C, long long sC,
                 long long ldcm, long long ldcn, int M, int N, long long K, int batch);
