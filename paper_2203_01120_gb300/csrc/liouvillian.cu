@@ -499,12 +499,14 @@ void alloc_workspace(QSlot &s, int nvec) {
   size_t p2 = (size_t)32 * batch * s.nb * s.nb;
   w.part.alloc(std::max(p1, p2) * c);
   w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
-  if (slab) {
+  if (slab)
     w.i2.reset();
-    w.coef.alloc(nv * 2 * 6 * (size_t)s.nr * sizeof(float2));
-  } else {
+  else
     w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
-  }
+  if (slab)
+    w.coef.alloc(nv * 2 * 6 * (size_t)s.nr * sizeof(float2));
+  else
+    w.coef.reset();
   w.nvec_cap = nvec;
   w.ready = true;
 }
@@ -785,7 +787,6 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   // its design and its nominal flops, accumulated by the profiler
   const double c = sizeof(cx<T>), re = sizeof(T);
   const double V = (double)br * nvec, G = (double)rows * nr, Gu = (double)s.rows() * nr;
-  const double fft_flops = (double)rows * 5.0 * nr * std::log2((double)nr);
   if (adj_mask) {  // L^H x = J L J x for the flagged vectors
     ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
     cx<T> *xin = w.xin.template as<cx<T>>();
@@ -801,9 +802,8 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   cx<T> *xr = w.xr.template as<cx<T>>();
   cx<T> *i1 = w.i1.template as<cx<T>>(), *i2 = w.i2.template as<cx<T>>();
   const bool slab = sizeof(T) == 4 && s.slab;
-  // pruned traffic: stick buffer (rows x nstick x n3) and plane buffer (rows x nplane x n2 x n3)
+  // pruned traffic of the plane-slab stages: stick buffer (rows x nstick x n3)
   const double S1 = (double)rows * s.nstick_max * s.fft[2];
-  const double S2 = (double)rows * s.nplane_max * s.fft[1] * s.fft[2];
   // FLOPs of the x-y line transforms of one pass on the slab path (planes + columns)
   const double xy_flops = (double)rows * s.fft[2] *
                           (s.nplane_max + s.fft[1]) * 5.0 * s.fft[0] * std::log2((double)s.fft[0]);
@@ -817,8 +817,7 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
       slab_inverse_yx(ctx, s, i1, xr, nvec);
     }
   } else {
-    ProfScope ps(pf, st, ST_FFT_INV, V * c + 2 * S1 * c + 2 * S2 * c + G * c, fft_flops);
-    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);
+    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);  // profiled per stage inside
   }
   // 2-4. densities and HXC potentials (one set per vector)
   cx<T> *rho = w.rho.template as<cx<T>>();
@@ -882,12 +881,9 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
                         nvec);
     }
   } else {
-    ProfScope ps(pf, st, ST_FFT_FWD,
-                 G * c + Gu * c + 4 * nvec * nr * (c + re) + 2 * S2 * c + 2 * S1 * c + 3 * V * c,
-                 fft_flops + (double)nbs * nr * 64.0);
     pipeline_forward<T>(ctx, s, x, xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(),
                         d.bfield.template as<T>(), vp, d.kin.template as<T>(),
-                        d.evals.template as<T>(), i1, i2, h, nvec);
+                        d.evals.template as<T>(), i1, i2, h, nvec);  // profiled inside
   }
   // 7. nonlocal pseudopotential (projector tables shared by all vectors: batch b -> k = b % nk)
   const long long bstride = (long long)nb * 2 * npwx;

@@ -396,6 +396,133 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+constexpr int kZThreads = 128;
+
+// ----------------------------------------------- register z lines (four-step)
+// A z line of length N = N1 * N2 is split over N1 neighbouring lanes: lane n1
+// transforms x[n1 + N1 n2] over n2 (N2 points, registers), multiplies by
+// w_N^(n1 k2), and the N1-point transforms across the lanes (warp shuffles) leave
+// lane n1 holding X[N2 k1 + k2] for one k1 and every k2:
+//   X[N2 k1 + k2] = sum_n1 w_N1^(n1 k1) w_N^(n1 k2) sum_n2 x[n1 + N1 n2] w_N2^(n2 k2).
+// For N1 = 4 the cross-lane transform is two radix-2 exchanges (even/odd n1, then
+// the halves), which leaves lane n1 with k1 = {0, 2, 1, 3}[n1].
+template <class T, int N1, int N2, int DIR>
+__device__ __forceinline__ int zline_fft(cx<T> (&a)[N2], int n1, const RegTw<T, N2> &tw2,
+                                         const RegTw<T, N1 * N2> &twn) {
+  constexpr int N = N1 * N2;
+  RegPlan<N2>::template run<T, DIR>(a, tw2);
+  if constexpr (N1 == 1) {
+    return 0;
+  } else {
+    static_assert(N1 == 4, "cross-lane radix");
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) {
+      cx<T> w = twn.w[(n1 * k2) % N];
+      if (DIR < 0) w.y = -w.y;
+      a[k2] = cmul<T>(a[k2], w);
+    }
+    const bool hi2 = (n1 & 2) != 0, odd = (n1 & 1) != 0;
+    // (A0 + A2, A1 + A3, A0 - A2, A1 - A3) on lanes 0..3
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      cx<T> p;
+      p.x = __shfl_xor_sync(0xffffffffu, a[k2].x, 2);
+      p.y = __shfl_xor_sync(0xffffffffu, a[k2].y, 2);
+      a[k2] = hi2 ? csub<T>(p, a[k2]) : cadd<T>(a[k2], p);
+    }
+    // X[c + 2d] = E_c + (-1)^d w4^c O_c : lane 0 -> X0, 1 -> X2, 2 -> X1, 3 -> X3
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      cx<T> p;
+      p.x = __shfl_xor_sync(0xffffffffu, a[k2].x, 1);
+      p.y = __shfl_xor_sync(0xffffffffu, a[k2].y, 1);
+      cx<T> o = odd ? a[k2] : p;  // O_c
+      const cx<T> e = odd ? p : a[k2];
+      if (hi2) o = DIR > 0 ? mk<T>(-o.y, o.x) : mk<T>(o.y, -o.x);  // w4^1 O_1
+      a[k2] = odd ? csub<T>(e, o) : cadd<T>(e, o);
+    }
+    return n1 == 0 ? 0 : n1 == 1 ? 2 : n1 == 2 ? 1 : 3;
+  }
+}
+
+// Inverse Z pass in registers: sphere coefficients gathered straight into the
+// lanes' registers, sticks written as [row][stick][j3] (TR = false) or
+// [row][j3][stick] (TR = true).
+template <class T, int N1, int N2, bool TR>
+__global__ void __launch_bounds__(kZThreads)
+    inv_z_reg_kernel(const cx<T> *__restrict__ x, cx<T> *__restrict__ i1,
+                     const int *__restrict__ nst, const int *__restrict__ smap, int nk, int nb,
+                     int npwx, int nsm, T scale, long long rows, const RegTw<T, N2> tw2,
+                     const RegTw<T, N1 * N2> twn) {
+  constexpr int N = N1 * N2, LPB = kZThreads / N1;
+  const long long row = row_of_block();
+  if (row >= rows) return;
+  const int k = (int)((row / (2 * nb)) % nk);
+  const int line = blockIdx.x * LPB + threadIdx.x / N1, n1 = threadIdx.x % N1;
+  const bool valid = line < __ldg(nst + k);
+  const int *mp = smap + ((long long)k * nsm + (valid ? line : 0)) * N;
+  const cx<T> *xrow = x + row * npwx;
+  cx<T> a[N2];
+#pragma unroll
+  for (int j = 0; j < N2; ++j) {
+    const int g = valid ? __ldg(mp + n1 + N1 * j) : -1;
+    a[j] = g >= 0 ? cscale<T>(xrow[g], scale) : czero<T>();
+  }
+  const int k1 = zline_fft<T, N1, N2, +1>(a, n1, tw2, twn);
+  if (!valid) return;
+  if (TR) {
+    cx<T> *o = i1 + row * N * (long long)nsm + line;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) o[(long long)(N2 * k1 + j) * nsm] = a[j];
+  } else {
+    cx<T> *o = i1 + (row * nsm + line) * N + N2 * k1;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) o[j] = a[j];
+  }
+}
+
+// Forward Z pass in registers, scattered to the sphere with + (kin - e) x.
+template <class T, int N1, int N2, bool TR>
+__global__ void __launch_bounds__(kZThreads)
+    fwd_z_reg_kernel(const cx<T> *__restrict__ i1, const cx<T> *__restrict__ x,
+                     cx<T> *__restrict__ h, const int *__restrict__ nst,
+                     const int *__restrict__ smap, const T *__restrict__ kin,
+                     const T *__restrict__ evals, int nk, int nb, int npwx, int nsm, T scale,
+                     long long rows, const RegTw<T, N2> tw2, const RegTw<T, N1 * N2> twn) {
+  constexpr int N = N1 * N2, LPB = kZThreads / N1;
+  const long long row = row_of_block();
+  if (row >= rows) return;
+  const int k = (int)((row / (2 * nb)) % nk);
+  const int line = blockIdx.x * LPB + threadIdx.x / N1, n1 = threadIdx.x % N1;
+  const bool valid = line < __ldg(nst + k);
+  const int ln = valid ? line : 0;
+  cx<T> a[N2];
+  if (TR) {
+    const cx<T> *src = i1 + row * N * (long long)nsm + ln;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) a[j] = valid ? src[(long long)(n1 + N1 * j) * nsm] : czero<T>();
+  } else {
+    const cx<T> *src = i1 + (row * nsm + ln) * N;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) a[j] = valid ? src[n1 + N1 * j] : czero<T>();
+  }
+  const int k1 = zline_fft<T, N1, N2, -1>(a, n1, tw2, twn);
+  if (!valid) return;
+  const int *mp = smap + ((long long)k * nsm + line) * N + N2 * k1;
+  const T e_n = evals[(row / 2) % (2LL * nk * nb)];
+  const T *kk = kin + (long long)k * npwx;
+  const cx<T> *xrow = x + row * npwx;
+  cx<T> *hrow = h + row * npwx;
+#pragma unroll
+  for (int j = 0; j < N2; ++j) {
+    const int g = __ldg(mp + j);
+    if (g < 0) continue;
+    const cx<T> xv = xrow[g];
+    const T d = kk[g] - e_n;
+    hrow[g] = mk<T>(a[j].x * scale + d * xv.x, a[j].y * scale + d * xv.y);
+  }
+}
+
 // ------------------------------------------- register-line variants (x, y axes)
 // One thread per line, the whole line in registers (regfft.cuh); neighbouring
 // threads own neighbouring lines, so each load/store of a warp is coalesced.
@@ -560,6 +687,35 @@ void set_smem(K kernel, size_t bytes) {
 
 constexpr int kTL = 16;
 
+// Register z-line plan for length n3: (lanes per line, points per lane), or (0, 0)
+// when n3 is neither a register length nor four times one.
+inline void z_plan(int n3, int &n1, int &n2) {
+  n1 = n2 = 0;
+  if (reg_fft_length(n3)) {
+    n1 = 1;
+    n2 = n3;
+  } else if (n3 % 4 == 0 && (n3 / 4 == 24 || n3 / 4 == 36 || n3 / 4 == 48)) {
+    n1 = 4;
+    n2 = n3 / 4;
+  }
+}
+
+// Launch ZKERNEL<T, N1, N2, TR> for the z plan (n1, n2); leaves ok = false otherwise.
+#define TDLZ_Z_LAUNCH(zn1, zn2, ZKERNEL, TRV, grid, ...)                                   \
+  do {                                                                                   \
+    ok = true;                                                                           \
+    if (zn1 == 1 && zn2 == 12) ZKERNEL<T, 1, 12, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 12>(), regtw<T, 12>()); \
+    else if (zn1 == 1 && zn2 == 16) ZKERNEL<T, 1, 16, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 16>(), regtw<T, 16>()); \
+    else if (zn1 == 1 && zn2 == 24) ZKERNEL<T, 1, 24, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 24>(), regtw<T, 24>()); \
+    else if (zn1 == 1 && zn2 == 36) ZKERNEL<T, 1, 36, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 36>(), regtw<T, 36>()); \
+    else if (zn1 == 1 && zn2 == 45) ZKERNEL<T, 1, 45, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 45>(), regtw<T, 45>()); \
+    else if (zn1 == 1 && zn2 == 48) ZKERNEL<T, 1, 48, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 48>(), regtw<T, 48>()); \
+    else if (zn1 == 4 && zn2 == 24) ZKERNEL<T, 4, 24, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 24>(), regtw<T, 96>()); \
+    else if (zn1 == 4 && zn2 == 36) ZKERNEL<T, 4, 36, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 36>(), regtw<T, 144>()); \
+    else if (zn1 == 4 && zn2 == 48) ZKERNEL<T, 4, 48, TRV><<<grid, kZThreads, 0, st>>>(__VA_ARGS__, regtw<T, 48>(), regtw<T, 192>()); \
+    else ok = false;                                                                     \
+  } while (0)
+
 // Register-line transforms: FP32 up to length 48, FP64 up to 45 (spill-free budget).
 template <class T> bool use_reg_lines(int n) {
   return reg_fft_length(n) && (sizeof(T) == 4 || n <= 45);
@@ -627,6 +783,27 @@ void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
   up(s.st_id, sid);
 }
 
+// Element counts and FLOPs of one pass over nvec stacked vectors, for the
+// profiler's algorithmic bytes (each stage's minimum traffic for its design).
+struct StageWork {
+  double V, S1, S2, G, Gu;                // BR, stick, plane, grid, U-grid elements
+  double z_flops, y_flops, x_flops;       // 5 N log2 N per line
+};
+template <class T> StageWork stage_work(const QSlot &s, int nvec) {
+  StageWork w;
+  const double rows = (double)s.rows() * nvec;
+  const int n1 = s.fft[0], n2 = s.fft[1], n3 = s.fft[2];
+  w.V = (double)s.br_elems() * nvec;
+  w.S1 = rows * s.nstick_max * n3;
+  w.S2 = rows * s.nplane_max * n2 * n3;
+  w.G = rows * s.nr;
+  w.Gu = (double)s.rows() * s.nr;
+  w.z_flops = rows * s.nstick_max * 5.0 * n3 * std::log2((double)n3);
+  w.y_flops = rows * s.nplane_max * n3 * 5.0 * n2 * std::log2((double)n2);
+  w.x_flops = rows * (double)n2 * n3 * 5.0 * n1 * std::log2((double)n1);
+  return w;
+}
+
 template <class T>
 void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *i1, cx<T> *i2,
                       int nvec) {
@@ -635,15 +812,32 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
   const long long rows = s.rows() * nvec, n23 = (long long)n2 * n3;
   const int nsm = s.nstick_max, npm = s.nplane_max;
   const size_t c = sizeof(cx<T>);
+  const StageWork wk = stage_work<T>(s, nvec);
+  bool ok = false;
   {
-    size_t sm = 2ull * n3 * (kTL + 1) * c;
-    set_smem(inv_z_kernel<T, kTL>, sm);
-    inv_z_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
-        x, i1, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
-        (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+    ProfScope ps(ctx.prof, st, ST_SCATTER, wk.V * c + wk.S1 * c, wk.z_flops);
+    int zn1, zn2;
+    z_plan(n3, zn1, zn2);
+    if (zn1) {
+      const int lpb = kZThreads / zn1;
+      dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
+      TDLZ_Z_LAUNCH(zn1, zn2, inv_z_reg_kernel, false, g, x, i1, s.st_n.as<int>(),
+                    s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, (T)(1.0 / std::sqrt(s.omega)),
+                    rows);
+    }
+    if (!ok) {
+      size_t sm = 2ull * n3 * (kTL + 1) * c;
+      set_smem(inv_z_kernel<T, kTL>, sm);
+      inv_z_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+          x, i1, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
+          (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+    }
     TDLZ_LAUNCH_CHECK();
   }
-  bool ok = use_reg_lines<T>(n2);
+  // sticks in, planes out and back in, real-space grids out
+  ProfScope ps(ctx.prof, st, ST_FFT_INV, wk.S1 * c + 2 * wk.S2 * c + wk.G * c,
+               wk.y_flops + wk.x_flops);
+  ok = use_reg_lines<T>(n2);
   if (ok) {
     dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n2, inv_y_reg_kernel, g, i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
@@ -684,19 +878,48 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
   const long long rows = s.rows() * nvec, nbs = rows / 2, n23 = (long long)n2 * n3;
   const int nsm = s.nstick_max, npm = s.nplane_max;
   const size_t c = sizeof(cx<T>);
+  const StageWork wk = stage_work<T>(s, nvec);
+  // potentials of every vector and the local fields, read once per point
+  const double pot_bytes = 4.0 * nvec * s.nr * (c + sizeof(T));
   bool ok = use_reg_lines<T>(n1);
   if (ok) {
-    // products in place (xr is not needed afterwards), then the X pass in registers
-    const long long nbs1 = nbs / nvec;
-    product_group_kernel<T><<<grid_rows((unsigned)((s.nr + 255) / 256), nbs1), 256, 0, st>>>(
-        const_cast<cx<T> *>(xr), ur, vloc, bf, v, s.nk, s.nb, s.nr, nvec);
-    TDLZ_LAUNCH_CHECK();
+    // products in place (xr is not needed afterwards): x(r) read and written, U(r)
+    // once per stacked group
+    {
+      ProfScope ps(ctx.prof, st, ST_PRODUCT, 2 * wk.G * c + wk.Gu * c + pot_bytes,
+                   (double)nbs * s.nr * 64.0);
+      const long long nbs1 = nbs / nvec;
+      product_group_kernel<T><<<grid_rows((unsigned)((s.nr + 255) / 256), nbs1), 256, 0, st>>>(
+          const_cast<cx<T> *>(xr), ur, vloc, bf, v, s.nk, s.nb, s.nr, nvec);
+      TDLZ_LAUNCH_CHECK();
+    }
+    ProfScope ps(ctx.prof, st, ST_FFT_FWD, wk.G * c + 2 * wk.S2 * c + wk.S1 * c,
+                 wk.x_flops + wk.y_flops);
     dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
     TDLZ_REG_LAUNCH(n1, fwd_x_reg_kernel, g, xr, i2, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
                     s.nr, rows);
     TDLZ_LAUNCH_CHECK();
-  }
-  if (!ok) {
+    ok = use_reg_lines<T>(n2);
+    if (ok) {
+      dim3 gy =
+          grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
+      TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
+                      s.nk, s.nb, nsm, npm, n3, rows);
+      TDLZ_LAUNCH_CHECK();
+    }
+    if (!ok) {
+      size_t sm = 2ull * n2 * (kTL + 1) * c;
+      set_smem(fwd_y_kernel<T, kTL>, sm);
+      fwd_y_kernel<T, kTL><<<grid_rows((n3 + kTL - 1) / kTL, rows * npm), 256, sm, st>>>(
+          i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
+          stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
+      TDLZ_LAUNCH_CHECK();
+    }
+  } else {
+    // X pass with the products formed in shared memory (no separate product pass)
+    ProfScope ps(ctx.prof, st, ST_FFT_FWD,
+                 wk.G * c + wk.Gu * c + pot_bytes + 2 * wk.S2 * c + wk.S1 * c,
+                 wk.x_flops + wk.y_flops + (double)nbs * s.nr * 64.0);
     size_t sm = 4ull * n1 * (kTL + 1) * c;
     set_smem(fwd_x_product_kernel<T, kTL>, sm);
     fwd_x_product_kernel<T, kTL><<<grid_rows((unsigned)((n23 + kTL - 1) / kTL), nbs), 256, sm,
@@ -704,29 +927,45 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
                                          s.pl_j1.as<int>(), s.nk, s.nb, npm, n1, n23, s.nr, nbs,
                                          stages(s.plan.ax[0]), tw_of<T>(s.plan.ax[0]));
     TDLZ_LAUNCH_CHECK();
-  }
-  ok = use_reg_lines<T>(n2);
-  if (ok) {
-    dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
-    TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, g, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
-                    s.nb, nsm, npm, n3, rows);
-    TDLZ_LAUNCH_CHECK();
-  }
-  if (!ok) {
-    size_t sm = 2ull * n2 * (kTL + 1) * c;
-    set_smem(fwd_y_kernel<T, kTL>, sm);
-    fwd_y_kernel<T, kTL><<<grid_rows((n3 + kTL - 1) / kTL, rows * npm), 256, sm, st>>>(
-        i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
-        stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
-    TDLZ_LAUNCH_CHECK();
+    ok = use_reg_lines<T>(n2);
+    if (ok) {
+      dim3 gy =
+          grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
+      TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
+                      s.nk, s.nb, nsm, npm, n3, rows);
+      TDLZ_LAUNCH_CHECK();
+    }
+    if (!ok) {
+      size_t smy = 2ull * n2 * (kTL + 1) * c;
+      set_smem(fwd_y_kernel<T, kTL>, smy);
+      fwd_y_kernel<T, kTL><<<grid_rows((n3 + kTL - 1) / kTL, rows * npm), 256, smy, st>>>(
+          i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
+          stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
+      TDLZ_LAUNCH_CHECK();
+    }
   }
   {
+    // sticks in; x read, h zeroed and written on the sphere
+    ProfScope ps(ctx.prof, st, ST_GATHER, wk.S1 * c + 3 * wk.V * c, wk.z_flops);
     TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * c, st));
-    size_t sm = 2ull * n3 * (kTL + 1) * c;
-    set_smem(fwd_z_gather_kernel<T, kTL>, sm);
-    fwd_z_gather_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
-        i1, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm, n3,
-        (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+    int zn1, zn2;
+    z_plan(n3, zn1, zn2);
+    ok = false;
+    if (zn1) {
+      const int lpb = kZThreads / zn1;
+      dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
+      TDLZ_Z_LAUNCH(zn1, zn2, fwd_z_reg_kernel, false, g, i1, x, h, s.st_n.as<int>(),
+                    s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
+                    (T)(std::sqrt(s.omega) / s.nr), rows);
+    }
+    if (!ok) {
+      size_t sm = 2ull * n3 * (kTL + 1) * c;
+      set_smem(fwd_z_gather_kernel<T, kTL>, sm);
+      fwd_z_gather_kernel<T, kTL><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+          i1, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
+          n3, (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]),
+          tw_of<T>(s.plan.ax[2]));
+    }
     TDLZ_LAUNCH_CHECK();
   }
 }
@@ -738,11 +977,23 @@ void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec
   const int n3 = s.fft[2];
   const long long rows = s.rows() * nvec;
   const int nsm = s.nstick_max;
-  size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
-  set_smem(inv_z_kernel<T, kTL, true>, sm);
-  inv_z_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
-      x, i1t, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
-      (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  int zn1, zn2;
+  z_plan(n3, zn1, zn2);
+  bool ok = false;
+  if (zn1) {
+    const int lpb = kZThreads / zn1;
+    dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
+    TDLZ_Z_LAUNCH(zn1, zn2, inv_z_reg_kernel, true, g, x, i1t, s.st_n.as<int>(),
+                  s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, (T)(1.0 / std::sqrt(s.omega)),
+                  rows);
+  }
+  if (!ok) {
+    size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
+    set_smem(inv_z_kernel<T, kTL, true>, sm);
+    inv_z_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+        x, i1t, s.st_n.as<int>(), s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, n3,
+        (T)(1.0 / std::sqrt(s.omega)), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  }
   TDLZ_LAUNCH_CHECK();
 }
 
@@ -754,11 +1005,23 @@ void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, co
   const long long rows = s.rows() * nvec;
   const int nsm = s.nstick_max;
   TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * sizeof(cx<T>), st));
-  size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
-  set_smem(fwd_z_gather_kernel<T, kTL, true>, sm);
-  fwd_z_gather_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
-      i1t, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm, n3,
-      (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  int zn1, zn2;
+  z_plan(n3, zn1, zn2);
+  bool ok = false;
+  if (zn1) {
+    const int lpb = kZThreads / zn1;
+    dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
+    TDLZ_Z_LAUNCH(zn1, zn2, fwd_z_reg_kernel, true, g, i1t, x, h, s.st_n.as<int>(),
+                  s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
+                  (T)(std::sqrt(s.omega) / s.nr), rows);
+  }
+  if (!ok) {
+    size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
+    set_smem(fwd_z_gather_kernel<T, kTL, true>, sm);
+    fwd_z_gather_kernel<T, kTL, true><<<grid_rows((nsm + kTL - 1) / kTL, rows), 256, sm, st>>>(
+        i1t, x, h, s.st_n.as<int>(), s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
+        n3, (T)(std::sqrt(s.omega) / s.nr), rows, stages(s.plan.ax[2]), tw_of<T>(s.plan.ax[2]));
+  }
   TDLZ_LAUNCH_CHECK();
 }
 

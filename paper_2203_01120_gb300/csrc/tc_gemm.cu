@@ -141,7 +141,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
                          | ((uint32_t)(nt >> 3) << 17)        // N >> 3
                          | ((uint32_t)(128 >> 4) << 24);      // M >> 4
   const float2 *Ab = g.A + (long long)a * g.sA;
-  const int sub = tid & (kChunks - 1), rstep = kRowStep;
+  // staging map: lanes 0-7 of a warp take 8 consecutive rows of one 16-byte chunk, so
+  // each group of 8 stores fills one 128-byte core-matrix row block (no bank conflicts);
+  // the 4 lane groups take 4 chunks, the warp pair (w, w^1) the other 4
+  const int lane = tid & 31;
+  const int sub = (lane >> 3) + 4 * (warp & 1);        // 16-byte chunk of the K tile
+  const int rbase = (warp >> 1) * 8 + (lane & 7);      // first row, then every kRowStep
+  const int rstep = kRowStep;
 
   for (int it = 0; it < nloc; ++it) {
     const int s = it & 1;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
     float4 va[kMaxA], vb[kMaxB];
 #pragma unroll
     for (int i = 0; i < kMaxA; ++i) {
-      const int m = tid / kChunks + i * rstep;
+      const int m = rbase + i * rstep;
       va[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m < g.M && kc < g.K) {
         const float2 *row = Ab + (long long)m * g.lda;
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
     }
 #pragma unroll
     for (int i = 0; i < kMaxB; ++i) {
-      const int r = tid / kChunks + i * rstep;
+      const int r = rbase + i * rstep;
       const int R = tile * nt + r;
       vb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r < nt && R < g.ntot && kc < g.K) {
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
     // A rows [A_int; A_rot]
 #pragma unroll
     for (int i = 0; i < kMaxA; ++i) {
-      const int m = tid / kChunks + i * rstep;
+      const int m = rbase + i * rstep;
       if (m < g.M) {
         float4 hi, lo;
         split4(va[i], hi, lo);
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
     // B rows of this N tile: stacked (j, n) -> batch a + j amod, row n
 #pragma unroll
     for (int i = 0; i < kMaxB; ++i) {
-      const int r = tid / kChunks + i * rstep;
+      const int r = rbase + i * rstep;
       if (r < nt) {
         float4 hi, lo;
         split4(vb[i], hi, lo);
