@@ -70,37 +70,53 @@ __device__ void block_sum_store(double2 (&v)[NV], double2 *out) {
 // this part FP64 arithmetic is ~1/64 of the FP32 rate, so the mixed path keeps
 // the per-element work in FP32 and only the reduction in FP64).
 constexpr int kRun = 16;
-template <class T>
+constexpr int kUnroll = 4;  // independent elements per thread per iteration (loads in flight)
+template <class T, int NP>
 __global__ void __launch_bounds__(kRedThreads)
     dots_kernel(Pairs pr, long long n, long long half, double2 *partial) {
   double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-  const int np = pr.n;
-  const cx<T> *A[4], *B[4];
-  T sgn[4];
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  const cx<T> *A[NP], *B[NP];
+  T sgn[NP];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < NP; ++i) {
     A[i] = reinterpret_cast<const cx<T> *>(pr.p[i].a);
     B[i] = reinterpret_cast<const cx<T> *>(pr.p[i].b);
     sgn[i] = pr.p[i].jsign ? T(-1) : T(1);
   }
+  const long long bd = blockDim.x;
   long long e = b0 + threadIdx.x;
+  // runs of kRun elements summed in T, each run added to the FP64 accumulators
   while (e < b1) {
-    T rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
-    for (int it = 0; it < kRun && e < b1; ++it, e += blockDim.x) {
-      bool neg = e >= half;
+    T rx[NP], ry[NP];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i >= np) break;
-        cx<T> a = A[i][e], b = B[i][e];
-        T s = neg ? sgn[i] : T(1);
-        rx[i] += s * (a.x * b.x + a.y * b.y);
-        ry[i] += s * (a.x * b.y - a.y * b.x);
+    for (int i = 0; i < NP; ++i) rx[i] = ry[i] = T(0);
+    for (int it = 0; it < kRun / kUnroll && e < b1; ++it) {
+      cx<T> av[kUnroll][NP], bv[kUnroll][NP];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long eu = e + u * bd;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          av[u][i] = eu < b1 ? A[i][eu] : czero<T>();
+          bv[u][i] = eu < b1 ? B[i][eu] : czero<T>();
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const bool neg = e + u * bd >= half;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const T sg = neg ? sgn[i] : T(1);
+          rx[i] += sg * (av[u][i].x * bv[u][i].x + av[u][i].y * bv[u][i].y);
+          ry[i] += sg * (av[u][i].x * bv[u][i].y - av[u][i].y * bv[u][i].x);
+        }
+      }
+      e += kUnroll * bd;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NP; ++i) {
       acc[i].x += (double)rx[i];
       acc[i].y += (double)ry[i];
     }
@@ -296,31 +312,51 @@ __global__ void __launch_bounds__(kRedThreads)
                                                             : cs->gamma_prev;
   const T ax = (T)a64.x, ay = (T)a64.y, gx = (T)g64.x, gy = (T)g64.y, bp = (T)cs->beta_prev;
   double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  const long long bd = blockDim.x;
+  const bool nh = flavor == TDLZ_NONHERMITIAN;
   long long e = b0 + threadIdx.x;
   while (e < b1) {
     T s0x = 0, s0y = 0, s1 = 0, s2 = 0;
-    for (int it = 0; it < kRun && e < b1; ++it, e += blockDim.x) {
-      cx<T> av = a[e], qv = q[e], qpv = qp[e];
-      cx<T> r = mk<T>(av.x - (ax * qv.x - ay * qv.y) - (gx * qpv.x - gy * qpv.y),
-                      av.y - (ax * qv.y + ay * qv.x) - (gx * qpv.y + gy * qpv.x));
-      qp[e] = r;
-      T rn = r.x * r.x + r.y * r.y;
-      if (flavor == TDLZ_NONHERMITIAN) {
-        cx<T> bv = b[e], pv = p[e], ppv = pp[e];
-        // t = b - conj(alpha) p - beta p'  (beta real)
-        cx<T> t = mk<T>(bv.x - (ax * pv.x + ay * pv.y) - bp * ppv.x,
-                        bv.y - (ax * pv.y - ay * pv.x) - bp * ppv.y);
-        pp[e] = t;
-        s0x += t.x * r.x + t.y * r.y;
-        s0y += t.x * r.y - t.y * r.x;
-        s1 += rn;
-        s2 += t.x * t.x + t.y * t.y;
-      } else {
-        s0x += e >= half ? -rn : rn;
-        s1 += rn;
+    for (int it = 0; it < kRun / kUnroll && e < b1; ++it) {
+      cx<T> av[kUnroll], qv[kUnroll], qpv[kUnroll], bv[kUnroll], pv[kUnroll], ppv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long eu = e + u * bd;
+        const bool in = eu < b1;
+        av[u] = in ? a[eu] : czero<T>();
+        qv[u] = in ? q[eu] : czero<T>();
+        qpv[u] = in ? qp[eu] : czero<T>();
+        if (nh) {
+          bv[u] = in ? b[eu] : czero<T>();
+          pv[u] = in ? p[eu] : czero<T>();
+          ppv[u] = in ? pp[eu] : czero<T>();
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const long long eu = e + u * bd;
+        if (eu >= b1) break;
+        const cx<T> r = mk<T>(av[u].x - (ax * qv[u].x - ay * qv[u].y) - (gx * qpv[u].x - gy * qpv[u].y),
+                              av[u].y - (ax * qv[u].y + ay * qv[u].x) - (gx * qpv[u].y + gy * qpv[u].x));
+        qp[eu] = r;
+        const T rn = r.x * r.x + r.y * r.y;
+        if (nh) {
+          // t = b - conj(alpha) p - beta p'  (beta real)
+          const cx<T> t = mk<T>(bv[u].x - (ax * pv[u].x + ay * pv[u].y) - bp * ppv[u].x,
+                                bv[u].y - (ax * pv[u].y - ay * pv[u].x) - bp * ppv[u].y);
+          pp[eu] = t;
+          s0x += t.x * r.x + t.y * r.y;
+          s0y += t.x * r.y - t.y * r.x;
+          s1 += rn;
+          s2 += t.x * t.x + t.y * t.y;
+        } else {
+          s0x += eu >= half ? -rn : rn;
+          s1 += rn;
+        }
+      }
+      e += kUnroll * bd;
     }
     acc[0].x += (double)s0x;
     acc[0].y += (double)s0y;
@@ -341,7 +377,12 @@ __global__ void jflip_kernel(const cx<T> *x, cx<T> *y, long long n, long long ha
 
 template <class T>
 void launch_dots(Context &ctx, Pairs pr, long long n, long long half, double2 *partial) {
-  dots_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial);
+  switch (pr.n) {
+    case 1: dots_kernel<T, 1><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+    case 2: dots_kernel<T, 2><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+    case 3: dots_kernel<T, 3><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+    default: dots_kernel<T, 4><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+  }
   TDLZ_LAUNCH_CHECK();
 }
 

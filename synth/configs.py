@@ -160,16 +160,41 @@ def _density(coeff, miller, npw, fft, omega, wk):
     return n0, m0
 
 
+def exchange_field(n0: np.ndarray, m0: np.ndarray) -> np.ndarray:
+    """Slater-exchange field of the self-consistent model, b(r) = g(n, |m|) m_hat with
+    g = (v_up - v_dn) / 2, v_s = -(6 n_s / pi)^(1/3), n_up/dn = (n +- |m|)/2 floored at
+    1e-4; b = 0 where n < 1e-10 or |m| < 1e-12 n (the SCF step of the model, the part
+    of the ground-state calculation the paper takes from pw.x)."""
+    c6 = (6.0 / np.pi) ** (1.0 / 3.0)
+    mabs = np.sqrt(np.sum(m0 * m0, axis=0))
+    nu = np.maximum(0.5 * (n0 + mabs), 1e-4)
+    nd = np.maximum(0.5 * (n0 - mabs), 1e-4)
+    g = 0.5 * (-c6 * nu ** (1.0 / 3.0) + c6 * nd ** (1.0 / 3.0))
+    ok = (n0 >= 1e-10) & (mabs >= 1e-12 * n0)
+    out = np.zeros_like(m0)
+    out[:, ok] = g[ok] * m0[:, ok] / mabs[ok]
+    return out
+
+
 def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = False,
                       kernel_mask: int = 3, device: str | None = None, tol: float = 1e-9,
                       ecut: float | None = None, q_2pi_a=None, nocc: int | None = None,
-                      dense_max: int = 2400, log=None, solver: str = "auto") -> GroundState:
+                      dense_max: int = 2400, log=None, solver: str = "auto",
+                      self_consistent: bool = False, b_ext: float = 0.0,
+                      scf_tol: float = 1e-11, scf_mix: float = 0.5,
+                      scf_iter: int = 400) -> GroundState:
     """Build the seeded ground-state bundle for config ``name``.
 
     collinear=True gives the special case of a uniform field along z with no
     spin-orbit coupling ([H, S_z] = 0).  solver="random" skips the
     diagonalisation and fills the occupied states with random orthonormal
     spinors (same shapes; for kernel profiling only, not a ground state).
+    self_consistent=True replaces the model field by the exchange field of the
+    ground state's own magnetisation (exchange_field) plus a uniform external field
+    b_ext along z, iterated with linear mixing until the field changes by less than
+    scf_tol (dense diagonalisation only).  With spin-orbit coupling off, a uniform
+    rotation of the magnetisation then precesses at exactly 2 b_ext (Larmor; zero
+    for b_ext = 0, the Goldstone case).
     """
     cfg = dataclasses.replace(CONFIGS[name])
     if seed is not None:
@@ -205,6 +230,9 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
     nk = kpts.shape[0]
     wk = np.full(nk, 1.0 / nk)
     q = np.array(cfg.q_2pi_a, dtype=np.float64) * 2 * np.pi / cfg.alat
+    if self_consistent:
+        bfield = _scf_field(cfg, kpts, wk, bvec, omega, fft, vloc, bfield, atoms, dnl, b_ext,
+                            scf_tol, scf_mix, scf_iter, dense_max)
     sph_k = [sphere(k, bvec, cfg.ecut, fft) for k in kpts]
     sph_kq = [sphere(k + q, bvec, cfg.ecut, fft) for k in kpts]
     npwx = max(max(s.shape[0] for s in sph_k), max(s.shape[0] for s in sph_kq))
@@ -279,6 +307,34 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
               "collinear": collinear},
     )
     return gs
+
+
+def _scf_field(cfg, kpts, wk, bvec, omega, fft, vloc, b_start, atoms, dnl, b_ext, scf_tol, mix,
+               niter, dense_max):
+    """Fixed point b = exchange_field(n0[b], m0[b]) + b_ext z by linear mixing (X side at k)."""
+    nb = cfg.nocc
+    b = b_start.copy()
+    sph = [sphere(k, bvec, cfg.ecut, fft) for k in kpts]
+    betas = [projector_values(k, mil, bvec, omega, atoms) for k, mil in zip(kpts, sph)]
+    for it in range(niter):
+        coeff = np.zeros((len(kpts), nb, 2, max(m.shape[0] for m in sph)), dtype=np.complex128)
+        for ik, (k, mil) in enumerate(zip(kpts, sph)):
+            if 2 * mil.shape[0] > dense_max:
+                raise ValueError("self-consistent model: dense diagonalisation only")
+            h = dense_hamiltonian(+1, k, mil, bvec, fft, vloc, b, betas[ik], dnl)
+            w, v = dense_lowest(h, nb + 1)
+            coeff[ik, :, :, :mil.shape[0]] = v[:, :nb].T.reshape(nb, 2, mil.shape[0])
+        miller = np.zeros((len(kpts), coeff.shape[-1], 3), dtype=np.int32)
+        for ik, mil in enumerate(sph):
+            miller[ik, :mil.shape[0]] = mil
+        n0, m0 = _density(coeff, miller, [m.shape[0] for m in sph], fft, omega, wk)
+        b_new = exchange_field(n0, m0)
+        b_new[2] += b_ext
+        change = float(np.max(np.abs(b_new - b)))
+        if change < scf_tol:
+            return b_new
+        b = (1.0 - mix) * b + mix * b_new
+    raise ValueError(f"self-consistent model: no convergence (last change {change:.2e})")
 
 
 def _iterative(torch, device, sgn, p, mil, bvec, fft, vloc, bfield, beta, dnl, nb, tol, rng, log,

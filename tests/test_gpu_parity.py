@@ -273,6 +273,47 @@ def test_structure_factor_matches_oracle(torch, ctx):
         ctx.structure_factor(chi, [0.0, 0.0, 0.0])
 
 
+def test_multi_q_chain_set_equals_separate_runs(torch, ctx):
+    """Batched form: chains on two q-slots (q and 2q) advance in one chain set (one
+    group per slot, both replayed from one captured graph) and reproduce the
+    single-slot runs coefficient for coefficient."""
+    from synth import make_ground_state
+    q1 = slot(ctx, "C0K")
+    q2 = ctx.load_ground_state(make_ground_state("C0K", q_2pi_a=(0.2, 0.0, 0.0)))
+    both = ctx.lanczos_run([q1, q2, q1, q2], [0, 0, 2, 2], 16, "nh")
+    for c, (qs, mu) in enumerate([(q1, 0), (q2, 0), (q1, 2), (q2, 2)]):
+        alone = ctx.lanczos_run([qs], [mu], 16, "nh")
+        for key in ("alpha", "beta", "gamma", "z", "n0"):
+            a, b = both[key][c], alone[key][0]
+            assert np.max(np.abs(a - b)) <= 1e-10 * np.max(np.abs(b)), (c, key)
+
+
+def test_larmor_mode_on_gpu(torch, ctx):
+    """The self-consistent collinear model with a uniform external field b_ext = 0.05
+    (no spin-orbit coupling): the GPU Liouvillian maps the brute-force Larmor
+    eigenvector to 2 b_ext times itself, and the NH chain started from sigma_x U has
+    a Ritz value at 2 b_ext."""
+    from synth import make_ground_state
+    from oracle.liouvillian import Liouvillian
+    from _bruteforce import ParticleHole
+    gs = make_ground_state("C0", collinear=True, kernel_mask=2, q_2pi_a=(1e-4, 0.0, 0.0),
+                           self_consistent=True, b_ext=0.05)
+    q = ctx.load_ground_state(gs)
+    lv = Liouvillian(gs)
+    ph = ParticleHole(gs, lv.fxc)
+    ev, vec = np.linalg.eig(ph.L)
+    i = int(np.argmin(np.abs(ev - 0.1)))
+    x = ph.to_br(vec[:, i])
+    y = apply_gpu(torch, ctx, q, x)
+    assert np.linalg.norm(y - 0.1 * x) <= 1e-7 * np.linalg.norm(x)
+    got = ctx.lanczos_run([q], [0], 30, "nh")
+    m = int(got["steps_done"][0])
+    t = np.diag(got["alpha"][0][:m]) + np.diag(got["beta"][0][:m - 1], -1) + np.diag(
+        got["gamma"][0][:m - 1], 1)
+    ritz = np.linalg.eigvals(t)
+    assert np.min(np.abs(ritz - 0.1)) <= 1e-6, np.sort(np.abs(ritz - 0.1))[:3]
+
+
 def test_restart_rejects_mismatched_image(torch, ctx):
     from paper_2203_01120_gb300 import TdlzError
     q = slot(ctx, "C1")

@@ -75,3 +75,36 @@ def test_independent_particle_eigenvalues():
     ev = np.sort(np.linalg.eigvals(ph.L).real)
     ref = np.sort(ph.J * ph.D)
     assert np.max(np.abs(ev - ref)) < 1e-11
+
+
+def _larmor_case(self_consistent):
+    from synth import make_ground_state
+    kw = dict(collinear=True, kernel_mask=2, q_2pi_a=(1e-4, 0.0, 0.0))
+    if self_consistent:
+        kw.update(self_consistent=True, b_ext=0.05)
+    return make_ground_state("C0", **kw)
+
+
+def test_larmor_mode_of_self_consistent_model():
+    """Physical pin of the transverse ALSDA kernel, the response densities and the
+    potential coupling: in a self-consistent collinear model without spin-orbit
+    coupling, with a uniform external field b_ext along z on top of the exchange
+    field of its own magnetisation, the uniform spin precession is an eigenmode of
+    L at exactly 2 b_ext (Larmor theorem; here at q -> 0, |q| = 1e-4 2pi/a).  The
+    same crystal with a fixed, non-self-consistent field has no such mode at 2|B|."""
+    from oracle.liouvillian import Liouvillian
+    from _bruteforce import ParticleHole
+    gs = _larmor_case(True)
+    lv = Liouvillian(gs)
+    ph = ParticleHole(gs, lv.fxc)
+    ev, vec = np.linalg.eig(ph.L)
+    i = int(np.argmin(np.abs(ev - 0.1)))
+    assert abs(ev[i] - 0.1) <= 1e-7, ev[i]
+    # the oracle's matrix-free L reproduces the eigenpair
+    x = ph.to_br(vec[:, i])
+    y = lv.apply(x)
+    assert np.linalg.norm(y - 0.1 * x) <= 1e-7 * np.linalg.norm(x)
+    gs2 = _larmor_case(False)
+    lv2 = Liouvillian(gs2)
+    ev2 = np.linalg.eigvals(ParticleHole(gs2, lv2.fxc).L)
+    assert np.min(np.abs(ev2 - 2 * 0.2)) > 1e-3
