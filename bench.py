@@ -61,7 +61,7 @@ def parse():
                     help="run N Liouvillian applications on a shape-only bundle (for profilers)")
     ap.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
     ap.add_argument("--kpoints", type=int, default=0,
-                    help="profile-apply: keep only the first N k points (smaller device footprint)")
+                    help="profiling runs only: keep the first N k points (smaller device footprint)")
     return ap.parse_args()
 
 
@@ -282,6 +282,8 @@ def run_tdlz(args):
     from paper_2203_01120_gb300 import TDLZ_FP64, TDLZ_MIXED, Context, build_ext
     build_ext.build()
     gs = make_workload(args.config, args.tol, args.bundle)
+    if args.kpoints:  # profiling captures only: the first k points of the workload
+        gs = sample_bundle(gs, args.kpoints)
     # replicas: every rank runs the chi columns mus (the paper's ipol = 4: x, y, z)
     mus = list(range(args.chains))
     stream = torch.cuda.Stream(device=local)

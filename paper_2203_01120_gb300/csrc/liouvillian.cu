@@ -139,16 +139,27 @@ void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *
   const int ppg = (npair + ngroup - 1) / ngroup;
   const int ng = (npair + ppg - 1) / ppg;
   const dim3 grid(blocks_for(nr), ng);
-  for (int v0 = 0; v0 < nvec; v0 += 3) {
-    const int nv = std::min(3, nvec - v0);
+  // up to 6 stacked vectors per pass in FP32 (3 in FP64: register budget), each pass
+  // reading U(r) once
+  const int vmax = sizeof(T) == 4 ? 6 : 3;
+  for (int v0 = 0; v0 < nvec; v0 += vmax) {
+    const int nv = std::min(vmax, nvec - v0);
     const cx<T> *xv = xr + (long long)v0 * rows1 * nr;
     cx<T> *pv = part + (long long)v0 * 4 * nr;
     if (nv == 1)
       density_kernel<T, 1><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
     else if (nv == 2)
       density_kernel<T, 2><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-    else
+    else if (nv == 3)
       density_kernel<T, 3><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
+    if constexpr (sizeof(T) == 4) {
+      if (nv == 4)
+        density_kernel<T, 4><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
+      else if (nv == 5)
+        density_kernel<T, 5><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
+      else if (nv == 6)
+        density_kernel<T, 6><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
+    }
     TDLZ_LAUNCH_CHECK();
   }
   long long n = (long long)nvec * 4 * nr;
@@ -295,8 +306,19 @@ __global__ void __launch_bounds__(NN_COLS)
   cx<T> acc[NN_ROWS];
 #pragma unroll
   for (int r = 0; r < NN_ROWS; ++r) acc[r] = czero<T>();
-  for (int kk = 0; kk < K; ++kk) {
-    cx<T> bv = Bb[(long long)kk * ldb + col];
+  // B column prefetched 8 entries at a time (independent loads in flight)
+  int kk = 0;
+  for (; kk + 8 <= K; kk += 8) {
+    cx<T> bv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) bv[u] = __ldg(Bb + (long long)(kk + u) * ldb + col);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r * K + kk + u], bv[u]);
+  }
+  for (; kk < K; ++kk) {
+    const cx<T> bv = __ldg(Bb + (long long)kk * ldb + col);
 #pragma unroll
     for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r * K + kk], bv);
   }

@@ -31,12 +31,12 @@ namespace tdlz {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
 constexpr int kKT = 32;                      // K tile: 32 reals (16 complex) = 128 bytes per row
 constexpr int kChunks = kKT / 4;             // 16-byte chunks per row in a K tile
 constexpr uint32_t kATile = 128 * kKT * 4;   // bytes of one A tile (hi or lo)
 constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
-constexpr int kRowStep = kTcThreads / kChunks;  // rows staged per pass (16)
+constexpr int kRowStep = kTcThreads / kChunks;  // rows staged per pass (32)
 constexpr int kMaxA = 64 / kRowStep;            // A rows per thread (M <= 64)
 constexpr int kMaxB = 256 / kRowStep;           // B rows per thread (N tile <= 256)
 
@@ -149,13 +149,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
   const int rbase = (warp >> 1) * 8 + (lane & 7);      // first row, then every kRowStep
   const int rstep = kRowStep;
 
-  for (int it = 0; it < nloc; ++it) {
-    const int s = it & 1;
-    const long long kc0 = (long long)(kt0 + it) * (kKT / 2);  // first complex index of the tile
-    const long long kc = kc0 + 2 * sub;                        // this thread's complex pair
-    // issue every global load of the tile first (read-only path), then split and store:
-    // loads interleaved with shared-memory stores would otherwise serialise
-    float4 va[kMaxA], vb[kMaxB];
+  // global loads of K tile t into registers (read-only path); issued one tile ahead
+  // of the shared-memory stores so that their latency overlaps the proxy fence, the
+  // barrier, the MMA issue and the wait for the stage
+  float4 va[kMaxA], vb[kMaxB];
+  auto load_tile = [&](int t) {
+    const long long kc = (long long)(kt0 + t) * (kKT / 2) + 2 * sub;  // complex pair
 #pragma unroll
     for (int i = 0; i < kMaxA; ++i) {
       const int m = rbase + i * rstep;
@@ -181,7 +180,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
         vb[i] = make_float4(t0.x, t0.y, t1.x, t1.y);
       }
     }
-    // the loads above are in flight while the MMAs of tile it-2 release stage s
+  };
+  if (nloc > 0) load_tile(0);
+  for (int it = 0; it < nloc; ++it) {
+    const int s = it & 1;
+    // tile it's loads are in flight while the MMAs of tile it-2 release stage s
     if (it >= 2) {
       if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
     }
@@ -214,6 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
         *reinterpret_cast<float4 *>(Blo + tile_off(r, sub, lboB)) = lo;
       }
     }
+    if (it + 1 < nloc) load_tile(it + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -250,12 +254,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const bool ok = !abort_flag && nloc > 0;
   if (!ok && tid == 0 && abort_flag) atomicExch(&g_tc_timeout, 1);
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
-  const int row = 32 * warp + (tid & 31);
+  // epilogue: warp w reads TMEM lanes (rows) 32 (w & 3) .. + 31 (its lane quarter),
+  // the two warps of a quarter take alternate 8-column chunks
+  const int quarter = warp & 3;
+  const int row = 32 * quarter + (tid & 31);
   float *out = g.part + ((((long long)z * gridDim.y + a) * g.ntiles + tile) * 128 + row) * nt;
-  for (int c0 = 0; c0 < nt; c0 += 8) {
+  for (int c0 = 8 * (warp >> 2); c0 < nt; c0 += 16) {
     uint32_t r[8];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
