@@ -240,6 +240,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per launch of a stage's kernel, from one ncu capture of the same build
+# (dram__bytes_read.sum + dram__bytes_write.sum): the product kernel of the C2 step
+# (6 stacked vectors) captured at 4 of the 16 k points, scaled by 4 (its traffic is
+# linear in the number of k points).  Summary: profiles/kernels_C2_k4_full.md.
+NCU_TRAFFIC = {("C2", "product"): 4 * 8.842e9}
+
+
+def ncu_traffic(args, stage):
+    if args.kpoints or args.flavor != "nh" or args.chains != 3:
+        return None
+    return NCU_TRAFFIC.get((args.config, stage))
+
+
 def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, stream, profile=False):
     """Chain-steps per second summed over the chains mus (one group on one q-slot).
     The library runs on `stream` (handed to it at context creation); the timed
@@ -365,8 +378,9 @@ def run_tdlz(args):
             "ms_per_step": 1000 * wall_fp64 / fp64_steps},
         "chi_rel_err": chi_err, "chi_steps": m, "chi_tolerance": 1e-4,
         "roofline": {"bound": "hbm", "stage": top, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src},
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": ncu_traffic(args, top), "traffic_unit": "bytes per launch",
+                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src},
         "step_roofline": {"alg_bytes_per_step": step_bytes, "ms_per_step_profiled": step_ms,
                           "achieved_gbs": step_bytes / (step_ms / 1000) / 1e9,
                           "frac_hbm": step_bytes / (step_ms / 1000) / 1e9 / hbm},

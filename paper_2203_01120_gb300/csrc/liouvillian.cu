@@ -139,27 +139,18 @@ void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *
   const int ppg = (npair + ngroup - 1) / ngroup;
   const int ng = (npair + ppg - 1) / ppg;
   const dim3 grid(blocks_for(nr), ng);
-  // up to 6 stacked vectors per pass in FP32 (3 in FP64: register budget), each pass
-  // reading U(r) once
-  const int vmax = sizeof(T) == 4 ? 6 : 3;
-  for (int v0 = 0; v0 < nvec; v0 += vmax) {
-    const int nv = std::min(vmax, nvec - v0);
+  // up to 3 stacked vectors per pass, each pass reading U(r) once (more vectors per
+  // pass raise the register count past two CTAs per SM and lose more than they save)
+  for (int v0 = 0; v0 < nvec; v0 += 3) {
+    const int nv = std::min(3, nvec - v0);
     const cx<T> *xv = xr + (long long)v0 * rows1 * nr;
     cx<T> *pv = part + (long long)v0 * 4 * nr;
     if (nv == 1)
       density_kernel<T, 1><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
     else if (nv == 2)
       density_kernel<T, 2><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-    else if (nv == 3)
+    else
       density_kernel<T, 3><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-    if constexpr (sizeof(T) == 4) {
-      if (nv == 4)
-        density_kernel<T, 4><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-      else if (nv == 5)
-        density_kernel<T, 5><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-      else if (nv == 6)
-        density_kernel<T, 6><<<grid, kThreads, 0, st>>>(ur, xv, wk, pv, nk, nb, nr, ppg, nvec);
-    }
     TDLZ_LAUNCH_CHECK();
   }
   long long n = (long long)nvec * 4 * nr;
