@@ -61,6 +61,7 @@ template <class T> struct SlotData {
   DevBuf ur;     // [2][nk][nb][2][Nr]   occupied k orbitals in real space
   DevBuf beta;   // [nk][nproj][npwx]
   DevBuf dnl;    // [2nproj][2nproj]
+  DevBuf dnl_val;  // [2nproj][dnl_w] nonzero entries of each row of D (ELL form)
   DevBuf kin;    // [nk][npwx]  |k+q+G|^2/2   (real)
   DevBuf evals;  // [2][nk][nb]               (real)
   DevBuf vloc;   // [Nr]   (real)
@@ -112,6 +113,8 @@ struct QSlot {
   DevBuf pl_j1;   // [nk][nplane_max] grid index j1 of each plane
   DevBuf pl_of;   // [nk][n1] plane index of j1 or -1
   DevBuf st_id;   // [nk][nplane_max][n2] stick index of (plane, j2) or -1
+  int dnl_w = 0;   // nonzeros per row of D in the ELL form (padded)
+  DevBuf dnl_col;  // [2nproj][dnl_w] column of each entry of dnl_val, -1 past the row's end
   bool slab = false;  // FP32 Liouvillian runs the plane-slab real-space stages (slab.cu)
   bool tensor_gemm = true;  // FP32 V_NL / P_c reductions on tcgen05 (tc_gemm.cu)
   FFTPlan plan;

@@ -275,7 +275,9 @@ __global__ void split_reduce_kernel(const cx<T> *__restrict__ part, cx<T> *__res
 constexpr int NN_ROWS = 16, NN_COLS = 128, NN_KMAX = 256;
 // grid: x = row chunk (fastest, so the CTAs that share a B column tile run together
 // and re-read it from L2), y = column chunk, z = batch; A chunk in dynamic smem.
-template <class T>
+// Each thread owns NC columns (tid + j NN_COLS, coalesced for every j), so every
+// shared-memory load of A feeds NC complex multiply-adds.
+template <class T, int NC>
 __global__ void __launch_bounds__(NN_COLS)
     gemm_nn_kernel(const cx<T> *__restrict__ A, long long sA, long long sar, long long sak,
                    const cx<T> *__restrict__ B, long long ldb, long long sB, int bmod,
@@ -291,42 +293,58 @@ __global__ void __launch_bounds__(NN_COLS)
     As[e] = (r0 + rr < rows) ? Ab[(long long)(r0 + rr) * sar + (long long)kk * sak] : czero<T>();
   }
   __syncthreads();
-  long long col = (long long)blockIdx.y * NN_COLS + threadIdx.x;
-  if (col >= ncol) return;
+  const long long col0 = (long long)blockIdx.y * NN_COLS * NC + threadIdx.x;
+  if (col0 >= ncol) return;
   const cx<T> *Bb = B + (long long)(b % bmod) * sB;
-  cx<T> acc[NN_ROWS];
+  cx<T> acc[NC][NN_ROWS];
 #pragma unroll
-  for (int r = 0; r < NN_ROWS; ++r) acc[r] = czero<T>();
-  // B column prefetched 8 entries at a time (independent loads in flight)
-  int kk = 0;
-  for (; kk + 8 <= K; kk += 8) {
-    cx<T> bv[8];
+  for (int j = 0; j < NC; ++j)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) bv[u] = __ldg(Bb + (long long)(kk + u) * ldb + col);
+    for (int r = 0; r < NN_ROWS; ++r) acc[j][r] = czero<T>();
+  // B columns prefetched 4 entries at a time (independent loads in flight)
+  constexpr int U = 4;
+  for (int kk = 0; kk < K; kk += U) {
+    cx<T> bv[U][NC];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r * K + kk + u], bv[u]);
-  }
-  for (; kk < K; ++kk) {
-    const cx<T> bv = __ldg(Bb + (long long)kk * ldb + col);
+      for (int j = 0; j < NC; ++j) {
+        const long long c = col0 + j * NN_COLS;
+        bv[u][j] = (kk + u < K && c < ncol) ? __ldg(Bb + (long long)(kk + u) * ldb + c)
+                                            : czero<T>();
+      }
 #pragma unroll
-    for (int r = 0; r < NN_ROWS; ++r) cfma<T>(acc[r], As[r * K + kk], bv);
+    for (int u = 0; u < U; ++u) {
+      if (kk + u >= K) break;
+#pragma unroll
+      for (int r = 0; r < NN_ROWS; ++r) {
+        const cx<T> av = As[r * K + kk + u];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) cfma<T>(acc[j][r], av, bv[u][j]);
+      }
+    }
   }
   T sg = (b % neg_mod) >= neg_from ? T(-1) : T(1);
 #pragma unroll
-  for (int r = 0; r < NN_ROWS; ++r) {
-    if (r0 + r >= rows) break;
-    long long o = (long long)b * sO + (long long)(r0 + r) * ldo + col;
-    cx<T> iv = In[o];
-    Out[o] = mk<T>(sg * (iv.x + alpha * acc[r].x), sg * (iv.y + alpha * acc[r].y));
+  for (int j = 0; j < NC; ++j) {
+    const long long col = col0 + j * NN_COLS;
+    if (col >= ncol) break;
+#pragma unroll
+    for (int r = 0; r < NN_ROWS; ++r) {
+      if (r0 + r >= rows) break;
+      long long o = (long long)b * sO + (long long)(r0 + r) * ldo + col;
+      cx<T> iv = In[o];
+      Out[o] = mk<T>(sg * (iv.x + alpha * acc[j][r].x), sg * (iv.y + alpha * acc[j][r].y));
+    }
   }
 }
 
-// dmix[b][(n,s)][i] = sum_{j,t} D[2i+s][2j+t] proj[b][j][(n,t)]
+// dmix[b][(n,s)][i] = sum_{j,t} D[2i+s][2j+t] proj[b][j][(n,t)], over the nonzero
+// entries of row 2i+s only (ELL form: D couples the projectors of one atom)
 template <class T>
-__global__ void dmix_kernel(const cx<T> *__restrict__ proj, const cx<T> *__restrict__ dnl,
-                            cx<T> *__restrict__ dmix, int nproj, int nb, int batch) {
+__global__ void dmix_kernel(const cx<T> *__restrict__ proj, const cx<T> *__restrict__ dval,
+                            const int *__restrict__ dcol, int dw, cx<T> *__restrict__ dmix,
+                            int nproj, int nb, int batch) {
   long long total = (long long)batch * nb * 2 * nproj;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -337,10 +355,13 @@ __global__ void dmix_kernel(const cx<T> *__restrict__ proj, const cx<T> *__restr
     int n = (int)(rest % nb);
     long long b = rest / nb;
     const cx<T> *pb = proj + b * (long long)nproj * 2 * nb;
-    const cx<T> *drow = dnl + (long long)(2 * i + s) * 2 * nproj;
+    const long long row = (long long)(2 * i + s) * dw;
     cx<T> acc = czero<T>();
-    for (int j = 0; j < nproj; ++j)
-      for (int t = 0; t < 2; ++t) cfma<T>(acc, drow[2 * j + t], pb[(long long)j * 2 * nb + 2 * n + t]);
+    for (int q = 0; q < dw; ++q) {
+      const int c = __ldg(dcol + row + q);
+      if (c < 0) break;
+      cfma<T>(acc, dval[row + q], pb[(long long)(c >> 1) * 2 * nb + 2 * n + (c & 1)]);
+    }
     dmix[e] = acc;
   }
 }
@@ -381,13 +402,16 @@ void gemm_nn(Context &ctx, const cx<T> *A, long long sA, long long sar, long lon
              long long ldo, long long sO, int rows, long long ncol, int K, T alpha, int batch,
              int neg_from, int neg_mod = 1 << 30) {
   TDLZ_REQUIRE(K <= NN_KMAX, TDLZ_ERR_ARG, "contraction length above 256 (nocc or nproj)");
-  dim3 grid((rows + NN_ROWS - 1) / NN_ROWS, (unsigned)((ncol + NN_COLS - 1) / NN_COLS), batch);
+  // two columns per thread in FP32, one in FP64 (register budget)
+  constexpr int NC = sizeof(T) == 4 ? 2 : 1;
+  dim3 grid((rows + NN_ROWS - 1) / NN_ROWS, (unsigned)((ncol + NN_COLS * NC - 1) / (NN_COLS * NC)),
+            batch);
   size_t sm = (size_t)NN_ROWS * K * sizeof(cx<T>);
-  TDLZ_CUDA_TRY(cudaFuncSetAttribute(gemm_nn_kernel<T>,
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(gemm_nn_kernel<T, NC>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  gemm_nn_kernel<T><<<grid, NN_COLS, sm, ctx.stream>>>(A, sA, sar, sak, B, ldb, sB, bmod, In, Out,
-                                                     ldo, sO, rows, ncol, K, alpha, neg_from,
-                                                     neg_mod);
+  gemm_nn_kernel<T, NC><<<grid, NN_COLS, sm, ctx.stream>>>(A, sA, sar, sak, B, ldb, sB, bmod, In,
+                                                         Out, ldo, sO, rows, ncol, K, alpha,
+                                                         neg_from, neg_mod);
   TDLZ_LAUNCH_CHECK();
 }
 
@@ -719,6 +743,33 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   if (np_ > 0) {
     up(d.beta, gs->beta_kq, (size_t)nk * np_ * npwx * sizeof(double2));
     up(d.dnl, gs->dnl, (size_t)4 * np_ * np_ * sizeof(double2));
+    // D is block diagonal over the atoms: keep each row's nonzero entries (ELL form)
+    const int nd = 2 * np_;
+    int w = 1;
+    for (int r = 0; r < nd; ++r) {
+      int cnt = 0;
+      for (int c = 0; c < nd; ++c) {
+        const double *v = gs->dnl + 2 * ((long long)r * nd + c);
+        cnt += (v[0] != 0.0 || v[1] != 0.0);
+      }
+      w = std::max(w, cnt);
+    }
+    std::vector<int> col((size_t)nd * w, -1);
+    std::vector<double> val((size_t)2 * nd * w, 0.0);
+    for (int r = 0; r < nd; ++r) {
+      int cnt = 0;
+      for (int c = 0; c < nd; ++c) {
+        const double *v = gs->dnl + 2 * ((long long)r * nd + c);
+        if (v[0] == 0.0 && v[1] == 0.0) continue;
+        col[(size_t)r * w + cnt] = c;
+        val[2 * ((size_t)r * w + cnt)] = v[0];
+        val[2 * ((size_t)r * w + cnt) + 1] = v[1];
+        ++cnt;
+      }
+    }
+    s.dnl_w = w;
+    up(s.dnl_col, col.data(), col.size() * sizeof(int));
+    up(d.dnl_val, val.data(), val.size() * sizeof(double));
   }
   up(d.kin, kin.data(), kin.size() * sizeof(double));
   up(d.evals, gs->evals, (size_t)2 * nk * nb * sizeof(double));
@@ -767,6 +818,7 @@ void ensure_precision(Context &ctx, QSlot &s) {
       if (s.nproj > 0) {
         convert_buf<float>(ctx, d.beta, f.beta);
         convert_buf<float>(ctx, d.dnl, f.dnl);
+        convert_buf<float>(ctx, d.dnl_val, f.dnl_val);
       }
       convert_buf<float>(ctx, d.kin, f.kin);
       convert_buf<float>(ctx, d.evals, f.evals);
@@ -917,8 +969,8 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
                  npwx, bstride, proj, (long long)np_ * 2 * nb, 2 * nb, 1, np_, 2 * nb, npwx,
                  batch);
     long long tot = (long long)batch * nb * 2 * np_;
-    dmix_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(proj, d.dnl.template as<cx<T>>(), dm,
-                                                        np_, nb, batch);
+    dmix_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
+        proj, d.dnl_val.template as<cx<T>>(), s.dnl_col.as<int>(), s.dnl_w, dm, np_, nb, batch);
     TDLZ_LAUNCH_CHECK();
     gemm_nn<T>(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<cx<T>>(), npwx,
                (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
