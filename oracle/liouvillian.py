@@ -86,8 +86,8 @@ class Liouvillian:
         """v'_a(r) = delta_a0 v'_H + sum_b f_ab rho'_b (Eqs. v_H_q, v_XC_q, b_XC_q)."""
         v = np.zeros_like(rho)
         if self.gs.kernel_mask & 1:
-            rg = np.fft.fftn(rho[0].reshape(self.fft)).ravel() / self.nr
-            vh = np.fft.ifftn((self.vh_fac * rg).reshape(self.fft)).ravel() * self.nr
+            rg = grid.fftn(rho[0].reshape(self.fft)).ravel() / self.nr
+            vh = grid.ifftn((self.vh_fac * rg).reshape(self.fft)).ravel() * self.nr
             v[0] += vh
         if self.gs.kernel_mask & 2:
             v += xc.apply_kernel(self.fxc, rho)
@@ -112,9 +112,12 @@ class Liouvillian:
         return np.einsum("ig,nis->nsg", beta, d)
 
     # ------------------------------------------------------------------ apply
-    def apply(self, x):
+    def apply(self, x, kpoints=None):
+        """L x.  kpoints (optional): compute the output only at these k points and leave
+        the rest zero; the response density still sums over every k point."""
         gs = self.gs
         x = np.asarray(x, dtype=np.complex128)
+        kset = range(gs.nk) if kpoints is None else sorted(set(int(k) for k in kpoints))
         rho = self.response_density(x)
         v = self.hxc_potential(rho)
         out = np.zeros_like(x)
@@ -128,7 +131,7 @@ class Liouvillian:
             h0 = SIGMA4[0][:, :, None] * self.vloc[None, None, :]
             for i in range(3):
                 h0 = h0 + s * PAULI[i][:, :, None] * self.bfield[i][None, None, :]
-            for k in range(gs.nk):
+            for k in kset:
                 npw = gs.npw_kq[k]
                 xs = x[side, k, :, :, :npw]
                 u = self.u_real(side, k)

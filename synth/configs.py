@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import dataclasses
 import numpy as np
+import scipy.fft
 
 from .model import (Atom, GroundState, KBChannel, PAULI, atom_dmatrix, block_diag,
                     cell_volume, miller_to_index, projector_values, reciprocal, sphere)
@@ -127,7 +128,7 @@ def _random_real_field(fft, bvec, gcut, sigma, rng):
     # Hermitian symmetry f(-G) = conj f(G): symmetrise
     neg = miller_to_index(-m, fft)
     coef = 0.5 * (coef + coef[neg].conj())
-    f = np.fft.ifftn(coef.reshape(fft)).ravel() * m.shape[0]
+    f = scipy.fft.ifftn(coef.reshape(fft), workers=-1).ravel() * m.shape[0]
     assert np.max(np.abs(f.imag)) < 1e-9 * max(1.0, np.max(np.abs(f.real)))
     return f.real.copy()
 
@@ -152,7 +153,7 @@ def _density(coeff, miller, npw, fft, omega, wk):
         for n in range(coeff.shape[1]):
             psi = np.zeros((2, nr), dtype=np.complex128)
             psi[:, idx] = coeff[k, n, :, :npw[k]]
-            psi = np.fft.ifftn(psi.reshape(2, *fft), axes=(1, 2, 3)).reshape(2, nr) * nr
+            psi = scipy.fft.ifftn(psi.reshape(2, *fft), axes=(1, 2, 3), workers=-1).reshape(2, nr) * nr
             psi /= np.sqrt(omega)
             n0 += wk[k] * np.sum(np.abs(psi) ** 2, axis=0)
             for i in range(3):

@@ -12,13 +12,14 @@ Two routes, both on the same discrete operator:
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft
 
 from .model import PAULI, miller_to_index
 
 
 def grid_fourier(f_r: np.ndarray, fft) -> np.ndarray:
     """F[m] = (1/Nr) sum_j f(r_j) exp(-i G_m.r_j) on the grid (C order, flat)."""
-    return np.fft.fftn(np.asarray(f_r).reshape(fft)).ravel() / np.prod(fft)
+    return scipy.fft.fftn(np.asarray(f_r).reshape(fft), workers=-1).ravel() / np.prod(fft)
 
 
 def dense_hamiltonian(sign: int, p: np.ndarray, miller: np.ndarray, bvec: np.ndarray,

@@ -30,6 +30,22 @@ def test_matrix_free_equals_bruteforce(name, mask):
     assert outside <= 1e-12 * np.linalg.norm(y)
 
 
+def test_apply_restricted_to_sampled_k_points():
+    """Outputs at a subset of k points (the density still over every k) equal the
+    brute-force L at those k points; the other k points stay zero."""
+    lv = liouvillian("C0K")
+    ph = particle_hole("C0K")
+    assert lv.gs.nk >= 2
+    rng = np.random.default_rng(17)
+    a = rng.standard_normal(ph.dim) + 1j * rng.standard_normal(ph.dim)
+    ref = ph.to_br(ph.L @ a)
+    ks = [lv.gs.nk - 1]
+    y = lv.apply(ph.to_br(a), kpoints=ks)
+    assert np.linalg.norm(y[:, ks] - ref[:, ks]) <= 1e-12 * np.linalg.norm(ref[:, ks])
+    rest = [k for k in range(lv.gs.nk) if k not in ks]
+    assert not y[:, rest].any()
+
+
 @pytest.mark.parametrize("name", ["C0", "C0K"])
 def test_adjoint_is_jlj(name):
     lv = liouvillian(name)
