@@ -116,7 +116,7 @@ struct QSlot {
   int dnl_w = 0;   // nonzeros per row of D in the ELL form (padded)
   DevBuf dnl_col;  // [2nproj][dnl_w] column of each entry of dnl_val, -1 past the row's end
   bool slab = false;  // FP32 Liouvillian runs the plane-slab real-space stages (slab.cu)
-  bool tensor_gemm = true;  // FP32 V_NL / P_c reductions on tcgen05 (tc_gemm.cu)
+  bool tensor_gemm = true;  // FP32 V_NL / P_c reductions and updates on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;
   SlotData<float> d32;

@@ -729,7 +729,7 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   // grid allows them; the staged pipeline is the default
   const char *slab_env = std::getenv("TDLZ_SLAB");
   s.slab = slab_supported(s) && slab_env && slab_env[0] == '1';
-  // TDLZ_TC=0 keeps the V_NL / P_c reductions on the CUDA-core GEMM (A/B timing)
+  // TDLZ_TC=0 keeps the V_NL / P_c reductions and updates on the CUDA-core GEMMs (A/B timing)
   const char *tc_env = std::getenv("TDLZ_TC");
   s.tensor_gemm = !(tc_env && tc_env[0] == '0');
   up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
@@ -972,9 +972,16 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
     dmix_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
         proj, d.dnl_val.template as<cx<T>>(), s.dnl_col.as<int>(), s.dnl_w, dm, np_, nb, batch);
     TDLZ_LAUNCH_CHECK();
-    gemm_nn<T>(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<cx<T>>(), npwx,
-               (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
-               batch);
+    bool tcu = false;
+    if constexpr (sizeof(T) == 4)
+      if (s.tensor_gemm)
+        tcu = tc_gemm_nn(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<float2>(),
+                         npwx, (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_,
+                         1.f, batch, batch, 1 << 30);
+    if (!tcu)
+      gemm_nn<T>(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<cx<T>>(), npwx,
+                 (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
+                 batch);
   }
   // 8. P_c and the row sign (occupied k+q states shared: batch b -> (side, k) = b % 2nk;
   //    Y-side batches (b % 2nk >= nk) negated)
@@ -991,8 +998,14 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
     if (!tc)
       gemm_tn<T>(ctx, w.part, ukq, 2LL * npwx, bstride, batch1, h, 2LL * npwx, bstride, ov,
                  (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
-    gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h, y,
-               2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk, batch1);
+    bool tcu = false;
+    if constexpr (sizeof(T) == 4)
+      if (s.tensor_gemm)
+        tcu = tc_gemm_nn(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h,
+                         y, 2LL * npwx, bstride, nb, 2LL * npwx, nb, -1.f, batch, nk, batch1);
+    if (!tcu)
+      gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h, y,
+                 2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk, batch1);
   }
   if (adj_mask) {
     ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);

@@ -311,6 +311,213 @@ __global__ void tc_reduce_kernel(const float *__restrict__ part, float2 *__restr
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Update GEMMs:  Out[b][r][n] = sg_b (In[b][r][n] + alpha sum_k A[b][r][k] B[b % bmod][k][n])
+//
+// computed transposed, so that one TMEM lane is one output column n: the MMA's M = 128
+// columns of B (rows (b.x, b.y) per complex k), its N = 2R rows built from A with
+// Re row 2r = (a.x, -a.y) and Im row 2r+1 = (a.y, a.x) per complex k, so that
+// D[n][2r] = Re (A B)[r][n] and D[n][2r+1] = Im (A B)[r][n] sit in neighbouring TMEM
+// columns of the same lane.  The epilogue thread of lane n then reads, updates and
+// writes row r of column n; a warp covers 32 consecutive n (coalesced).
+constexpr int kNnKT = 16;                 // K tile: 16 reals (8 complex) = 64 bytes per row
+constexpr int kNnM = 128;                 // output columns per CTA (the MMA's M)
+
+struct NnArgs {
+  const float2 *A;
+  long long sA, sar, sak;
+  const float2 *B;
+  long long ldb, sB;
+  int bmod;
+  const float2 *In;
+  float2 *Out;
+  long long ldo, sO;
+  long long ncol;
+  int R, K, nm, nkt;   // output rows, complex K, the MMA's N (2R rounded up to 16), K tiles
+  float alpha;
+  int neg_from, neg_mod;
+  uint32_t tmem_cols;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long ct = blockIdx.x;  // column tile
+  const long long b = blockIdx.y;   // batch
+  const uint32_t lboA = (kNnM / 8) * 128, lboB = (uint32_t)(g.nm / 8) * 128;
+  const uint32_t aTile = kNnM * kNnKT * 4, bTile = (uint32_t)g.nm * kNnKT * 4;
+  const uint32_t stage_bytes = 2 * aTile + 2 * bTile;
+
+  // zero both stages once (B-operand rows >= 2R stay zero)
+  for (uint32_t i = tid; i < 2 * stage_bytes / 16; i += blockDim.x)
+    reinterpret_cast<float4 *>(tc_smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(g.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = (1u << 4)                           // D: F32
+                         | (2u << 7) | (2u << 10)             // A, B: TF32
+                         | ((uint32_t)(g.nm >> 3) << 17)      // N >> 3
+                         | ((uint32_t)(kNnM >> 4) << 24);     // M >> 4
+  const float2 *Bb = g.B + (b % g.bmod) * g.sB;
+  const float2 *Ab = g.A + b * g.sA;
+  // staging items: the MMA's A operand has 128 rows x 4 chunks (two per thread, lanes on
+  // consecutive columns n: coalesced loads, 16-byte stores at a 16-byte stride); its
+  // B operand has R x 4 (row r, chunk) items, each writing rows 2r and 2r+1
+  float4 va[2], vb[2];
+  auto load_tile = [&](int t) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * kTcThreads;
+      const int i = e & (kNnM - 1), c = e >> 7;
+      const long long n = ct * kNnM + i;
+      const int kc = t * (kNnKT / 2) + 2 * c;
+      float2 t0 = make_float2(0.f, 0.f), t1 = t0;
+      if (n < g.ncol) {
+        if (kc < g.K) t0 = __ldg(Bb + (long long)kc * g.ldb + n);
+        if (kc + 1 < g.K) t1 = __ldg(Bb + (long long)(kc + 1) * g.ldb + n);
+      }
+      va[u] = make_float4(t0.x, t0.y, t1.x, t1.y);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * kTcThreads;
+      const int r = e >> 2, c = e & 3;
+      const int kc = t * (kNnKT / 2) + 2 * c;
+      float2 t0 = make_float2(0.f, 0.f), t1 = t0;
+      if (r < g.R) {
+        if (kc < g.K) t0 = __ldg(Ab + r * g.sar + kc * g.sak);
+        if (kc + 1 < g.K) t1 = __ldg(Ab + r * g.sar + (kc + 1) * g.sak);
+      }
+      vb[u] = make_float4(t0.x, t0.y, t1.x, t1.y);
+    }
+  };
+  if (g.nkt > 0) load_tile(0);
+  for (int it = 0; it < g.nkt; ++it) {
+    const int s = it & 1;
+    if (it >= 2) {
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    unsigned char *st = tc_smem + (size_t)s * stage_bytes;
+    unsigned char *Ahi = st, *Alo = st + aTile, *Bhi = st + 2 * aTile, *Blo = Bhi + bTile;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * kTcThreads;
+      const int i = e & (kNnM - 1), c = e >> 7;
+      float4 hi, lo;
+      split4(va[u], hi, lo);
+      *reinterpret_cast<float4 *>(Ahi + tile_off(i, c, lboA)) = hi;
+      *reinterpret_cast<float4 *>(Alo + tile_off(i, c, lboA)) = lo;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * kTcThreads;
+      const int r = e >> 2, c = e & 3;
+      if (r < g.R) {
+        const float4 v = vb[u];
+        float4 hi, lo;
+        split4(make_float4(v.x, -v.y, v.z, -v.w), hi, lo);  // Re row: (a.x, -a.y)
+        *reinterpret_cast<float4 *>(Bhi + tile_off(2 * r, c, lboB)) = hi;
+        *reinterpret_cast<float4 *>(Blo + tile_off(2 * r, c, lboB)) = lo;
+        split4(make_float4(v.y, v.x, v.w, v.z), hi, lo);    // Im row: (a.y, a.x)
+        *reinterpret_cast<float4 *>(Bhi + tile_off(2 * r + 1, c, lboB)) = hi;
+        *reinterpret_cast<float4 *>(Blo + tile_off(2 * r + 1, c, lboB)) = lo;
+      }
+    }
+    if (it + 1 < g.nkt) load_tile(it + 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi),
+                     bl = smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < kNnKT / 8; ++ks) {
+        const uint32_t oa = 2 * ks * lboA, ob = 2 * ks * lboB;
+        const uint64_t dah = smem_desc(ah + oa, lboA, 128), dal = smem_desc(al + oa, lboA, 128);
+        const uint64_t dbh = smem_desc(bh + ob, lboB, 128), dbl = smem_desc(bl + ob, lboB, 128);
+        const uint32_t acc0 = (it > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.eq.u32 p, 1, 1;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %4, %5, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbl), "r"(idesc), "l"(dal), "l"(dbh));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar[s])));
+    }
+  }
+  if (g.nkt > 0 && !abort_flag) {
+    const int last = g.nkt - 1;
+    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_flag = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = !abort_flag;
+  if (abort_flag && tid == 0) atomicExch(&g_tc_timeout, 1);
+  // epilogue: warp w reads lane quarter w & 3 (32 consecutive columns n); the two warps
+  // of a quarter take alternate 16-column TMEM blocks (8 output rows each)
+  const int quarter = warp & 3;
+  const long long n = ct * kNnM + 32 * quarter + lane;
+  const bool nv = n < g.ncol;
+  const float sg = (b % g.neg_mod) >= g.neg_from ? -1.f : 1.f;
+  const float2 *inb = g.In + b * g.sO + n;
+  float2 *outb = g.Out + b * g.sO + n;
+  for (int j0 = 16 * (warp >> 2); j0 < 2 * g.R; j0 += 32) {
+    const int r0 = j0 >> 1;
+    float2 iv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      iv[u] = (nv && r0 + u < g.R) ? inb[(long long)(r0 + u) * g.ldo] : make_float2(0.f, 0.f);
+    uint32_t v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (ok && nv) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (r0 + u >= g.R) break;
+        const float re = __uint_as_float(v[2 * u]), im = __uint_as_float(v[2 * u + 1]);
+        outb[(long long)(r0 + u) * g.ldo] =
+            make_float2(sg * (iv[u].x + g.alpha * re), sg * (iv[u].y + g.alpha * im));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(g.tmem_cols));
+}
+
 }  // namespace
 
 bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
@@ -355,6 +562,48 @@ bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, l
   tc_reduce_kernel<<<blocks_for(total), 256, 0, ctx.stream>>>(g.part, C, M, N, amod, g.nj,
                                                                g.ntiles, g.nt, g.nsplit, sC,
                                                                ldcm, ldcn);
+  TDLZ_LAUNCH_CHECK();
+  return true;
+}
+
+bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long long sak,
+                const float2 *B, long long ldb, long long sB, int bmod, const float2 *In,
+                float2 *Out, long long ldo, long long sO, int rows, long long ncol, int K,
+                float alpha, int batch, int neg_from, int neg_mod) {
+  if (rows < 1 || 2 * rows > 256 || K < 1 || ncol < 1 || batch < 1 || bmod < 1 || neg_mod < 1)
+    return false;
+  NnArgs g;
+  g.A = A;
+  g.sA = sA;
+  g.sar = sar;
+  g.sak = sak;
+  g.B = B;
+  g.ldb = ldb;
+  g.sB = sB;
+  g.bmod = bmod;
+  g.In = In;
+  g.Out = Out;
+  g.ldo = ldo;
+  g.sO = sO;
+  g.ncol = ncol;
+  g.R = rows;
+  g.K = K;
+  g.nm = (2 * rows + 15) / 16 * 16;
+  g.nkt = (K + kNnKT / 2 - 1) / (kNnKT / 2);
+  g.alpha = alpha;
+  g.neg_from = neg_from;
+  g.neg_mod = neg_mod;
+  g.tmem_cols = 32;
+  while (g.tmem_cols < (uint32_t)g.nm) g.tmem_cols *= 2;
+  const size_t stage = 2 * (size_t)kNnM * kNnKT * 4 + 2 * (size_t)g.nm * kNnKT * 4;
+  // no more CTAs per SM than the 512 TMEM columns hold: ask for enough shared memory
+  // that one more would not fit either (228 KB per SM, 1 KB reserved per CTA)
+  const int cap = (int)(512 / g.tmem_cols);
+  const size_t smem = std::max(2 * stage, (size_t)(233472 / (cap + 1)));
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_nn_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((ncol + kNnM - 1) / kNnM), (unsigned)batch);
+  tc_gemm_nn_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(g);
   TDLZ_LAUNCH_CHECK();
   return true;
 }

@@ -13,6 +13,16 @@ bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, l
                 int amod, const float2 *B, long long ldb, long long sB, float2 *C, long long sC,
                 long long ldcm, long long ldcn, int M, int N, long long K, int batch);
 
+// Out[b*sO + r*ldo + n] = sg_b (In[...] + alpha sum_k A[b*sA + r*sar + k*sak]
+//                                           B[(b % bmod)*sB + k*ldb + n])
+// for b < batch, r < rows, n < ncol, k < K (complex FP32, 3xTF32 on the tensor cores,
+// FP32 accumulation); sg_b = -1 where b % neg_mod >= neg_from, else +1.  In may equal
+// Out (in-place update).  Returns false, launching nothing, for 2 rows > 256.
+bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long long sak,
+                const float2 *B, long long ldb, long long sB, int bmod, const float2 *In,
+                float2 *Out, long long ldo, long long sO, int rows, long long ncol, int K,
+                float alpha, int batch, int neg_from, int neg_mod);
+
 // Throws TDLZ_ERR_TIMEOUT (and clears the flag) if a tensor-core GEMM gave up on an
 // mbarrier wait since the last check.  Synchronous.
 void tc_gemm_check();
