@@ -445,6 +445,20 @@ __device__ __forceinline__ int zline_fft(cx<T> (&a)[N2], int n1, const RegTw<T, 
   }
 }
 
+// Shared-memory staging of the inverse pass's [row][stick][j3] output (FP32, four
+// lanes per line): a warp's LW = 8 lines go to global memory as one contiguous block
+// (full 32-byte sectors) instead of 8-byte stores strided over four lanes (each lane
+// holds X[N2 k1 + j] for its own k1).  The forward pass reads x[n1 + 4 n2], four
+// consecutive elements per line and instruction, already whole sectors.
+// Position p = N2 k1 + j of line l sits at l S + k1 (N2 + 1) + j; with S = 4 (N2 + 1)
+// (= 4 mod 16 for N2 = 0 mod 4) both the per-lane accesses and the block copies are
+// free of bank conflicts.
+template <class T, int N1, int N2, bool TR> struct ZStage {
+  static constexpr bool on = sizeof(T) == 4 && N1 == 4 && N2 <= 36 && !TR;
+  static constexpr int LW = 32 / N1, S = N1 * (N2 + 1);
+  static constexpr int IT = LW * N1 * N2 / 32;  // block elements per lane (= N2)
+};
+
 // Inverse Z pass in registers: sphere coefficients gathered straight into the
 // lanes' registers, sticks written as [row][stick][j3] (TR = false) or
 // [row][j3][stick] (TR = true).
@@ -469,6 +483,25 @@ __global__ void __launch_bounds__(kZThreads)
     a[j] = g >= 0 ? cscale<T>(xrow[g], scale) : czero<T>();
   }
   const int k1 = zline_fft<T, N1, N2, +1>(a, n1, tw2, twn);
+  if constexpr (ZStage<T, N1, N2, TR>::on) {
+    // the warp's lines through shared memory, then one contiguous block per warp
+    using Z = ZStage<T, N1, N2, TR>;
+    __shared__ cx<T> zs[kZThreads / 32][Z::LW * Z::S];
+    cx<T> *ws = zs[threadIdx.x >> 5];
+    const int ll = (threadIdx.x & 31) / N1, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) ws[ll * Z::S + k1 * (N2 + 1) + j] = a[j];
+    __syncwarp();
+    const int l0 = blockIdx.x * LPB + (threadIdx.x >> 5) * Z::LW;
+    const int nv = min(max(__ldg(nst + k) - l0, 0), Z::LW);
+    cx<T> *o = i1 + (row * nsm + l0) * N;
+#pragma unroll
+    for (int i = 0; i < Z::IT; ++i) {
+      const int e = lane + 32 * i, l = e / N, p = e - l * N, q = p / N2;
+      if (e < nv * N) o[e] = ws[l * Z::S + q * (N2 + 1) + (p - q * N2)];
+    }
+    return;
+  }
   if (!valid) return;
   if (TR) {
     cx<T> *o = i1 + row * N * (long long)nsm + line;
