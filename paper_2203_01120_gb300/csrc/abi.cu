@@ -200,9 +200,11 @@ tdlz_status tdlz_apply_liouvillian(tdlz_ctx *ctx, int qslot, const void *x, void
                      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged),
                  TDLZ_ERR_ARG, "y is not device memory");
     if (precision == TDLZ_FP64)
-      apply_liouvillian<double>(ctx->c, s, (const double2 *)x, (double2 *)y, 1, adjoint ? 1u : 0u);
+      apply_liouvillian_caller_order<double>(ctx->c, s, (const double2 *)x, (double2 *)y,
+                                             adjoint != 0);
     else
-      apply_liouvillian<float>(ctx->c, s, (const float2 *)x, (float2 *)y, 1, adjoint ? 1u : 0u);
+      apply_liouvillian_caller_order<float>(ctx->c, s, (const float2 *)x, (float2 *)y,
+                                            adjoint != 0);
   });
 }
 

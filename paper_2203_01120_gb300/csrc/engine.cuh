@@ -101,6 +101,12 @@ struct QSlot {
   double q[3];
   std::vector<int> npw_k, npw_kq;
   std::vector<double> wk;
+  // Every k+q-sphere array on the device (BR vectors, kin, beta, occupied k+q states,
+  // idx_kq, map_kq_k, st_map) uses the internal plane-wave order: ascending grid index,
+  // i.e. stick by stick with j3 ascending inside a stick.  perm[k][i] is the caller's
+  // index of internal plane wave i; iperm[k][g] the internal index of caller index g.
+  DevBuf perm, iperm;    // [nk][npwx] int32 (-1 beyond npw_kq)
+  DevBuf io_x, io_y;     // caller-order <-> internal-order scratch of the apply entry point
   DevBuf idx_k, idx_kq;  // [nk][npwx] int32 grid index (-1 beyond npw)
   DevBuf map_kq_k;       // [nk][npwx] int32: index of the same G in the k sphere or -1
   DevBuf npwkq_d;        // [nk] int32
@@ -157,6 +163,10 @@ template <class T>
 void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nvec,
                        unsigned adj_mask);
 template <class T> void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v);
+// y = L x (or L^H x) for one vector in the caller's plane-wave order (x, y device).
+template <class T>
+void apply_liouvillian_caller_order(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y,
+                                    bool adjoint);
 void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs);
 
 // --- allocation-free spectrum (spectrum_noalloc.cu) ---

@@ -13,6 +13,7 @@
 //   6  forward 3D FFT, gather to the k+q sphere, + (|k+q+G|^2/2 - e_n) x
 //   7  V_NL: <beta|x> (split-K reduction GEMM), D mixing, beta (D <beta|x>)
 //   8  P_c: <U_m|h> (split-K reduction GEMM), h - U <U|h>, row sign (Y side -)
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -660,6 +661,48 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
       map[(size_t)k * npwx + g] = it == where.end() ? -1 : it->second;
     }
   }
+  // ---- internal plane-wave order of the k+q spheres: ascending grid index (stick by
+  // stick, j3 ascending inside a stick), so that the Z passes read and write contiguous
+  // runs of each stick; perm[k][i] = caller index of internal index i
+  std::vector<int> perm((size_t)nk * npwx, -1), iperm((size_t)nk * npwx, -1);
+  for (int k = 0; k < nk; ++k) {
+    const int npw = gs->npw_kq[k];
+    int *pk = perm.data() + (size_t)k * npwx;
+    const int *id = idx_kq.data() + (size_t)k * npwx;
+    for (int i = 0; i < npw; ++i) pk[i] = i;
+    std::sort(pk, pk + npw, [id](int a, int b) { return id[a] < id[b]; });  // ids distinct
+    for (int i = 0; i < npw; ++i) iperm[(size_t)k * npwx + pk[i]] = i;
+  }
+  // [outer][nk][rows][npwx] complex arrays in the internal order (zero padding)
+  auto to_internal = [&](const double *src, long long outer, long long rws) {
+    std::vector<double> dst((size_t)(outer * nk * rws * npwx * 2), 0.0);
+    for (long long o = 0; o < outer; ++o)
+      for (int k = 0; k < nk; ++k) {
+        const int *pk = perm.data() + (size_t)k * npwx;
+        for (long long r = 0; r < rws; ++r) {
+          const size_t base = (size_t)(((o * nk + k) * rws + r) * npwx) * 2;
+          for (int i = 0; i < gs->npw_kq[k]; ++i) {
+            dst[base + 2 * i] = src[base + 2 * (size_t)pk[i]];
+            dst[base + 2 * i + 1] = src[base + 2 * (size_t)pk[i] + 1];
+          }
+        }
+      }
+    return dst;
+  };
+  {
+    std::vector<int> ip((size_t)nk * npwx, -1), mp((size_t)nk * npwx, -1);
+    for (int k = 0; k < nk; ++k)
+      for (int i = 0; i < gs->npw_kq[k]; ++i) {
+        const size_t g = (size_t)k * npwx + perm[(size_t)k * npwx + i];
+        ip[(size_t)k * npwx + i] = idx_kq[g];
+        mp[(size_t)k * npwx + i] = map[g];
+      }
+    idx_kq.swap(ip);
+    map.swap(mp);
+  }
+  const std::vector<double> ukq_int = to_internal(gs->coeff_kq, 2, 2LL * nb);
+  const std::vector<double> beta_int =
+      np_ > 0 ? to_internal(gs->beta_kq, 1, np_) : std::vector<double>();
   // ---- host-side geometry
   s.nk = nk;
   s.nb = nb;
@@ -693,12 +736,12 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   s.wk.assign(gs->wk, gs->wk + nk);
   std::vector<double> kin((size_t)nk * npwx, 0.0);
   for (int k = 0; k < nk; ++k)
-    for (int g = 0; g < gs->npw_kq[k]; ++g) {
-      const int *m = gs->miller_kq + 3 * ((long long)k * npwx + g);
+    for (int i = 0; i < gs->npw_kq[k]; ++i) {
+      const int *m = gs->miller_kq + 3 * ((long long)k * npwx + perm[(size_t)k * npwx + i]);
       double v[3];
       for (int c = 0; c < 3; ++c)
         v[c] = gs->kpts[3 * k + c] + gs->q[c] + m[0] * bv[0][c] + m[1] * bv[1][c] + m[2] * bv[2][c];
-      kin[(size_t)k * npwx + g] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      kin[(size_t)k * npwx + i] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     }
   // Hartree factor on the grid: 4 pi/|q+G|^2 / Nr where |q+G|^2/2 <= 4 ecut
   std::vector<double> vh(nr, 0.0);
@@ -732,16 +775,18 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   // TDLZ_TC=0 keeps the V_NL / P_c reductions and updates on the CUDA-core GEMMs (A/B timing)
   const char *tc_env = std::getenv("TDLZ_TC");
   s.tensor_gemm = !(tc_env && tc_env[0] == '0');
+  up(s.perm, perm.data(), perm.size() * sizeof(int));
+  up(s.iperm, iperm.data(), iperm.size() * sizeof(int));
   up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
   up(s.idx_kq, idx_kq.data(), idx_kq.size() * sizeof(int));
   up(s.map_kq_k, map.data(), map.size() * sizeof(int));
   up(s.npwkq_d, gs->npw_kq, nk * sizeof(int));
   SlotData<double> &d = s.d64;
   size_t brb = (size_t)s.br_elems() * sizeof(double2);
-  up(d.ukq, gs->coeff_kq, brb);
+  up(d.ukq, ukq_int.data(), brb);
   up(s.coeff_k, gs->coeff_k, brb);
   if (np_ > 0) {
-    up(d.beta, gs->beta_kq, (size_t)nk * np_ * npwx * sizeof(double2));
+    up(d.beta, beta_int.data(), (size_t)nk * np_ * npwx * sizeof(double2));
     up(d.dnl, gs->dnl, (size_t)4 * np_ * np_ * sizeof(double2));
     // D is block diagonal over the atoms: keep each row's nonzero entries (ELL form)
     const int nd = 2 * np_;
@@ -1047,6 +1092,38 @@ void start_vector(Context &ctx, QSlot &s, int mu, cx<T> *v) {
   TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+// caller order <-> internal order of one BR vector: out[row][i] = in[row][idx[k][i]]
+// (idx = perm: caller -> internal; idx = iperm: internal -> caller), zero where idx < 0
+template <class T>
+__global__ void permute_rows_kernel(const cx<T> *__restrict__ in, cx<T> *__restrict__ out,
+                                    const int *__restrict__ idx, int nk, int nb, int npwx,
+                                    long long nrows) {
+  const long long row = blockIdx.y + (long long)gridDim.y * blockIdx.z;
+  if (row >= nrows) return;
+  const int k = (int)((row / (2 * nb)) % nk);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npwx; i += gridDim.x * blockDim.x) {
+    const int g = idx[(long long)k * npwx + i];
+    out[row * npwx + i] = g >= 0 ? in[row * npwx + g] : czero<T>();
+  }
+}
+
+template <class T>
+void apply_liouvillian_caller_order(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y,
+                                    bool adjoint) {
+  const size_t bytes = (size_t)s.br_elems() * sizeof(cx<T>);
+  if (s.io_x.bytes < bytes) s.io_x.alloc(bytes);
+  if (s.io_y.bytes < bytes) s.io_y.alloc(bytes);
+  cx<T> *xi = s.io_x.as<cx<T>>(), *yi = s.io_y.as<cx<T>>();
+  const dim3 g = row_grid(s.rows(), s.npwx);
+  permute_rows_kernel<T><<<g, kThreads, 0, ctx.stream>>>(x, xi, s.perm.as<int>(), s.nk, s.nb,
+                                                         s.npwx, s.rows());
+  TDLZ_LAUNCH_CHECK();
+  apply_liouvillian<T>(ctx, s, xi, yi, 1, adjoint ? 1u : 0u);
+  permute_rows_kernel<T><<<g, kThreads, 0, ctx.stream>>>(yi, y, s.iperm.as<int>(), s.nk, s.nb,
+                                                         s.npwx, s.rows());
+  TDLZ_LAUNCH_CHECK();
+}
+
 template void ensure_precision<double>(Context &, QSlot &);
 template void ensure_precision<float>(Context &, QSlot &);
 template void apply_liouvillian<double>(Context &, QSlot &, const double2 *, double2 *, int,
@@ -1055,5 +1132,9 @@ template void apply_liouvillian<float>(Context &, QSlot &, const float2 *, float
                                        unsigned);
 template void start_vector<double>(Context &, QSlot &, int, double2 *);
 template void start_vector<float>(Context &, QSlot &, int, float2 *);
+template void apply_liouvillian_caller_order<double>(Context &, QSlot &, const double2 *,
+                                                     double2 *, bool);
+template void apply_liouvillian_caller_order<float>(Context &, QSlot &, const float2 *,
+                                                    float2 *, bool);
 
 }  // namespace tdlz

@@ -445,11 +445,12 @@ __device__ __forceinline__ int zline_fft(cx<T> (&a)[N2], int n1, const RegTw<T, 
   }
 }
 
-// Shared-memory staging of the inverse pass's [row][stick][j3] output (FP32, four
-// lanes per line): a warp's LW = 8 lines go to global memory as one contiguous block
-// (full 32-byte sectors) instead of 8-byte stores strided over four lanes (each lane
-// holds X[N2 k1 + j] for its own k1).  The forward pass reads x[n1 + 4 n2], four
-// consecutive elements per line and instruction, already whole sectors.
+// Shared-memory staging of the register Z passes (FP32, four lanes per line).  Each
+// lane ends its transform holding X[N2 k1 + j] for its own k1.  The inverse pass
+// writes a warp's LW = 8 lines of the [row][stick][j3] buffer as one contiguous block
+// (full 32-byte sectors instead of 8-byte stores strided over four lanes); the forward
+// pass transposes so that lane n1 holds X[n1 + 4 j] and the four lanes of a line
+// scatter to consecutive plane waves (the k+q spheres are stored stick by stick).
 // Position p = N2 k1 + j of line l sits at l S + k1 (N2 + 1) + j; with S = 4 (N2 + 1)
 // (= 4 mod 16 for N2 = 0 mod 4) both the per-lane accesses and the block copies are
 // free of bank conflicts.
@@ -540,12 +541,37 @@ __global__ void __launch_bounds__(kZThreads)
     for (int j = 0; j < N2; ++j) a[j] = valid ? src[n1 + N1 * j] : czero<T>();
   }
   const int k1 = zline_fft<T, N1, N2, -1>(a, n1, tw2, twn);
-  if (!valid) return;
-  const int *mp = smap + ((long long)k * nsm + line) * N + N2 * k1;
   const T e_n = evals[(row / 2) % (2LL * nk * nb)];
   const T *kk = kin + (long long)k * npwx;
   const cx<T> *xrow = x + row * npwx;
   cx<T> *hrow = h + row * npwx;
+  if constexpr (ZStage<T, N1, N2, TR>::on) {
+    // transpose through shared memory so that lane n1 holds X[n1 + N1 j]: the four lanes
+    // of a line then scatter to consecutive plane waves of the stick (j3 ascending)
+    using Z = ZStage<T, N1, N2, TR>;
+    __shared__ cx<T> zs[kZThreads / 32][Z::LW * Z::S];
+    cx<T> *ws = zs[threadIdx.x >> 5];
+    const int ll = (threadIdx.x & 31) / N1;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) ws[ll * Z::S + k1 * (N2 + 1) + j] = a[j];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < N2; ++j)
+      a[j] = ws[ll * Z::S + (N1 * j / N2) * (N2 + 1) + (N1 * j) % N2 + n1];
+    if (!valid) return;
+    const int *mp = smap + ((long long)k * nsm + line) * N + n1;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) {
+      const int g = __ldg(mp + N1 * j);
+      if (g < 0) continue;
+      const cx<T> xv = xrow[g];
+      const T d = kk[g] - e_n;
+      hrow[g] = mk<T>(a[j].x * scale + d * xv.x, a[j].y * scale + d * xv.y);
+    }
+    return;
+  }
+  if (!valid) return;
+  const int *mp = smap + ((long long)k * nsm + line) * N + N2 * k1;
 #pragma unroll
   for (int j = 0; j < N2; ++j) {
     const int g = __ldg(mp + j);
