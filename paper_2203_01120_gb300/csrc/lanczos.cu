@@ -14,6 +14,9 @@
 //  NH   q1 = p1 = v/||v||; a = L q, b = L^H p; alpha = p^H a;
 //       r = a - alpha q - gamma q',  t = b - conj(alpha) p - conj(beta) p';
 //       c = t^H r, beta' = sqrt|c|, gamma' = c / beta', q = r/beta', p = t/conj(gamma').
+//       The left vectors are stored as p~ = J p: then L^H p = J L p~, so one plain L
+//       pass over [q.., p~..] gives a and b~ = J b, the recursion for t~ = J t has the
+//       same form, and p^H a = p~^H J a, t^H r = t~^H J r (no sign-flip passes).
 //  PH   J metric: c0 = v^H J v, q1 = v/sqrt|c0|, s1 = sign c0; a = L q;
 //       alpha = s Re(q^H J a); r = a - alpha q - gamma q'; c = r^H J r,
 //       beta' = sqrt|c|, s' = sign c, gamma' = s s' beta'.
@@ -299,7 +302,8 @@ __global__ void scale_kernel(cx<T> *x, const double2 *scale, long long n) {
 }
 
 // r = a - alpha q - g q'  (written over q'); partial dots of (r, r)_J, (r, r).
-// NH also: t = b - conj(alpha) p - conj(beta) p' (over p'); dots (t, r), (r, r), (t, t).
+// NH also: t~ = b~ - conj(alpha) p~ - conj(beta) p~' (over p~'); dots (t~, r)_J = (t, r),
+// (r, r), (t~, t~) = (t, t).
 template <class T>
 __global__ void __launch_bounds__(kRedThreads)
     update_kernel(const cx<T> *a, const cx<T> *q, cx<T> *qp, const cx<T> *b, const cx<T> *p,
@@ -347,8 +351,9 @@ __global__ void __launch_bounds__(kRedThreads)
           const cx<T> t = mk<T>(bv[u].x - (ax * pv[u].x + ay * pv[u].y) - bp * ppv[u].x,
                                 bv[u].y - (ax * pv[u].y - ay * pv[u].x) - bp * ppv[u].y);
           pp[eu] = t;
-          s0x += t.x * r.x + t.y * r.y;
-          s0y += t.x * r.y - t.y * r.x;
+          const T sg = eu >= half ? T(-1) : T(1);
+          s0x += sg * (t.x * r.x + t.y * r.y);
+          s0y += sg * (t.x * r.y - t.y * r.x);
           s1 += rn;
           s2 += t.x * t.x + t.y * t.y;
         } else {
@@ -401,7 +406,7 @@ template void jflip_copy<float>(Context &, QSlot &, const float2 *, float2 *);
 // Chains on the same q-slot form a group whose vectors are stacked so that one
 // Liouvillian pass serves them all (the occupied orbitals are read once per pass).
 // Vector slots of a group (m members; each slot holds a block of vectors):
-//   NH : 0 [q_1..q_m, p_1..p_m]  1 [q'.., p'..]  2 [a.., b..]   (L on q, L^H on p)
+//   NH : 0 [q_1..q_m, p~_1..p~_m]  1 [q'.., p~'..]  2 [a.., b~..]   (one L pass, p~ = J p)
 //   PH : 0 [q..]  1 [q'..]  2 [a..]
 //   PHM: 0 [q..]  1 [q'.. / r..]  2 [Lq..]  3 [w..]
 template <class T>
@@ -468,9 +473,8 @@ void ChainSet::init_impl() {
                                                                 &cs->scale_q, n);
         TDLZ_LAUNCH_CHECK();
       }
-      if (flavor == TDLZ_NONHERMITIAN)  // p_1 = q_1
-        TDLZ_CUDA_TRY(cudaMemcpyAsync((cx<T> *)gr.slot[0] + (m + mi) * n, Q, n * c,
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
+      if (flavor == TDLZ_NONHERMITIAN)  // p~_1 = J q_1
+        jflip_copy<T>(*ctx, s, Q, (cx<T> *)gr.slot[0] + (m + mi) * n);
     }
     if (flavor == TDLZ_PSEUDOHERMITIAN_POSDEF) std::swap(gr.slot[2], gr.slot[3]);  // Lq = w / n0
   }
@@ -488,10 +492,9 @@ void ChainSet::advance_impl(int nsteps) {
       const cx<T> *u = slot_data<T>(s).uvec.template as<cx<T>>();
       cx<T> *S0 = (cx<T> *)gr.slot[0], *S1 = (cx<T> *)gr.slot[1], *S2 = (cx<T> *)gr.slot[2];
       if (flavor == TDLZ_NONHERMITIAN) {
-        // a = L q and b = L^H p for every member in one pass
-        const unsigned mask = ((1u << m) - 1u) << m;  // m <= 16 (checked at creation)
-        apply_liouvillian<T>(*ctx, s, S0, S2, 2 * m, mask);
-        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 20.0 * m * n * sizeof(cx<T>),
+        // a = L q and b~ = L p~ = J L^H p for every member in one pass
+        apply_liouvillian<T>(*ctx, s, S0, S2, 2 * m, 0u);
+        ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 18.0 * m * n * sizeof(cx<T>),
                      40.0 * m * n);
         for (int mi = 0; mi < m; ++mi) {
           Chain &ch = chains[gr.members[mi]];
@@ -500,7 +503,7 @@ void ChainSet::advance_impl(int nsteps) {
                 *PP = S1 + (m + mi) * n, *A = S2 + mi * n, *B = S2 + (m + mi) * n;
           Pairs pr{};
           pr.n = 4;
-          pr.p[0] = Pair{P, A, 0};
+          pr.p[0] = Pair{P, A, 1};  // p^H a = p~^H J a
           for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
           launch_dots<T>(*ctx, pr, n, half, part);
           scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
