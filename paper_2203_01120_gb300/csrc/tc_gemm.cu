@@ -32,11 +32,11 @@ namespace tdlz {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kKT = 32;                      // K tile: 32 reals (16 complex) = 128 bytes per row
+constexpr int kKT = 16;                      // K tile: 16 reals (8 complex) = 64 bytes per row
 constexpr int kChunks = kKT / 4;             // 16-byte chunks per row in a K tile
 constexpr uint32_t kATile = 128 * kKT * 4;   // bytes of one A tile (hi or lo)
 constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier waits
-constexpr int kRowStep = kTcThreads / kChunks;  // rows staged per pass (32)
+constexpr int kRowStep = kTcThreads / kChunks;  // rows staged per pass (64)
 constexpr int kMaxA = 64 / kRowStep;            // A rows per thread (M <= 64)
 constexpr int kMaxB = 256 / kRowStep;           // B rows per thread (N tile <= 256)
 
@@ -101,7 +101,7 @@ struct TcArgs {
   float *part;     // [nsplit][amod][ntiles][128][nt]
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs g) {
+__global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = g.nt;
   const uint32_t lboA = 16 * 128, lboB = (uint32_t)(nt / 8) * 128;
+  static_assert(kKT / 8 >= 1 && kChunks % 4 == 0, "K tile of whole MMA steps, 4-chunk groups");
   const uint32_t bTile = (uint32_t)nt * kKT * 4;
   const uint32_t stage_bytes = 2 * kATile + 2 * bTile;
   // CTA coordinates: x = N tile, y = A batch, z = K split
@@ -143,10 +144,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_tn_kernel(const TcArgs 
   const float2 *Ab = g.A + (long long)a * g.sA;
   // staging map: lanes 0-7 of a warp take 8 consecutive rows of one 16-byte chunk, so
   // each group of 8 stores fills one 128-byte core-matrix row block (no bank conflicts);
-  // the 4 lane groups take 4 chunks, the warp pair (w, w^1) the other 4
+  // the 4 lane groups take 4 chunks, kChunks / 4 consecutive warps the K tile's chunks
+  constexpr int kWarpsPerRow = kChunks / 4;
   const int lane = tid & 31;
-  const int sub = (lane >> 3) + 4 * (warp & 1);        // 16-byte chunk of the K tile
-  const int rbase = (warp >> 1) * 8 + (lane & 7);      // first row, then every kRowStep
+  const int sub = (lane >> 3) + 4 * (warp % kWarpsPerRow);   // 16-byte chunk
+  const int rbase = (warp / kWarpsPerRow) * 8 + (lane & 7);  // first row; then every kRowStep
   const int rstep = kRowStep;
 
   // global loads of K tile t into registers (read-only path); issued one tile ahead
@@ -541,11 +543,11 @@ bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, l
   g.nt = ((g.ntot + g.ntiles - 1) / g.ntiles + 15) / 16 * 16;
   g.nkt = (int)((K + kKT / 2 - 1) / (kKT / 2));
   const int ctas = amod * g.ntiles;
-  // about two waves of one-CTA-per-SM work, within the split-K scratch
+  // about two waves of two CTAs per SM, within the split-K scratch
   const size_t per_split = (size_t)amod * g.ntiles * 128 * g.nt * sizeof(float);
   const long long fit = (long long)(partbuf.bytes / per_split);
   if (fit < 1) return false;
-  long long ns = std::max(1, std::min(g.nkt, (2 * 152 + ctas - 1) / ctas));
+  long long ns = std::max(1, std::min(g.nkt, (4 * 152 + ctas - 1) / ctas));
   ns = std::min(ns, fit);
   g.kt_per_split = (int)((g.nkt + ns - 1) / ns);
   g.nsplit = (g.nkt + g.kt_per_split - 1) / g.kt_per_split;
