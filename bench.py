@@ -339,6 +339,7 @@ def run_tdlz(args):
         c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)
         chi_err = max(float(np.linalg.norm(c32[i] - c64[i]) / np.linalg.norm(c64[i][mu]))
                       for i, mu in enumerate(mus))
+    autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     ctx.close()
     if rank != 0:
         return
@@ -387,7 +388,7 @@ def run_tdlz(args):
         "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
         "stages_fp64_ms_per_step": {k: round(v["ms"] / fp64_steps, 4) for k, v in prof64.items()
                                     if v["launches"]},
-        "clocks": clocks, "gpu_launches": launches,
+        "clocks": clocks, "gpu_launches": launches, "autotune": autotune,
         "e2e": {"value": len(mus) * args.steps / e2e_wall, "unit": "steps/s",
                 "h2d_bytes_per_step": bundle_bytes / args.steps,
                 "d2h_bytes_per_step": coef_bytes / args.steps,

@@ -264,6 +264,15 @@ const char *tdlz_stage_name(int stage);
 /* Kernels launched by this library in this process so far. */
 int64_t tdlz_launch_count(void);
 
+/* Autotuner decisions of this context so far, one "stage/shape=choice (ms)" line per
+ * tuned stage and shape (threads per CTA of the register-line FFT passes, vectors per
+ * density pass).  Every candidate computes identical results; the first eager call
+ * with a new shape times each candidate on the context stream and keeps the fastest.
+ * TDLZ_AUTOTUNE=0 in the environment at tdlz_create keeps the defaults.  Writes at most
+ * len bytes including the terminating NUL into the caller's host buffer buf and the
+ * full length (without NUL) into *needed (may be NULL).  Host-only, no launch. */
+tdlz_status tdlz_autotune_report(tdlz_ctx *ctx, char *buf, int64_t len, int64_t *needed);
+
 #ifdef __cplusplus
 }
 #endif

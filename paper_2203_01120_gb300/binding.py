@@ -92,6 +92,8 @@ EXPORTS = {
     "tdlz_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "tdlz_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), _dp, _dp]),
     "tdlz_stage_name": (C.c_char_p, [C.c_int]),
+    "tdlz_autotune_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64,
+                                       C.POINTER(C.c_int64)]),
     "tdlz_launch_count": (C.c_int64, []),
 }
 NSTAGE = 11
@@ -222,6 +224,19 @@ class Context:
 
     def launch_count(self):
         return int(self.lib.tdlz_launch_count())
+
+    def autotune_report(self):
+        """{"stage/shape": (choice, ms)} of the autotuner's decisions so far."""
+        need = C.c_int64()
+        self._check(self.lib.tdlz_autotune_report(self.h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value + 1)
+        self._check(self.lib.tdlz_autotune_report(self.h, buf, need.value + 1, C.byref(need)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            key, _, rest = line.rpartition("=")
+            val, _, ms = rest.partition(" (")
+            out[key] = (int(val), float(ms.rstrip(" ms)")))
+        return out
 
     def vec_layout(self, qslot):
         n = C.c_int64()

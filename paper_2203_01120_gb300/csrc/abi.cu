@@ -2,6 +2,7 @@
 // arguments on the host, runs inside a try block and maps failures to a
 // tdlz_status with a message for tdlz_last_error(); no C++ exception crosses
 // the boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -76,6 +77,9 @@ tdlz_status tdlz_create(tdlz_ctx **out, int device, void *cuda_stream) {
     delete ctx;
     return TDLZ_ERR_CUDA;
   }
+  // TDLZ_AUTOTUNE=0 keeps every tunable stage at its default launch shape
+  const char *at = std::getenv("TDLZ_AUTOTUNE");
+  ctx->c.tuner.on = !(at && at[0] == '0');
   if (cuda_stream) {
     ctx->c.stream = (cudaStream_t)cuda_stream;
   } else {
@@ -154,6 +158,19 @@ tdlz_status tdlz_structure_factor(tdlz_ctx *ctx, const double *chi, int nomega,
 const char *tdlz_stage_name(int stage) { return stage_name(stage); }
 
 int64_t tdlz_launch_count(void) { return g_launches.load(); }
+
+tdlz_status tdlz_autotune_report(tdlz_ctx *ctx, char *buf, int64_t len, int64_t *needed) {
+  return guarded(ctx, [&] {
+    TDLZ_REQUIRE(len >= 0 && (buf || len == 0), TDLZ_ERR_ARG, "NULL buffer with len > 0");
+    const std::string r = ctx->c.tuner.report();
+    if (needed) *needed = (int64_t)r.size();
+    if (len > 0) {
+      const size_t n = std::min((size_t)(len - 1), r.size());
+      std::memcpy(buf, r.data(), n);
+      buf[n] = '\0';
+    }
+  });
+}
 
 tdlz_status tdlz_synchronize(tdlz_ctx *ctx) {
   return guarded(ctx, [&] {

@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "profile.cuh"
+#include "tuner.cuh"
 
 namespace tdlz {
 
@@ -140,6 +141,7 @@ struct Context {
   std::string last_error;
   std::vector<std::unique_ptr<QSlot>> slots;
   Profiler prof;
+  Tuner tuner;
 };
 
 template <class T> inline SlotData<T> &slot_data(QSlot &s) {

@@ -15,6 +15,7 @@
 //   8  P_c: <U_m|h> (split-K reduction GEMM), h - U <U|h>, row sign (Y side -)
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <unordered_map>
@@ -130,8 +131,14 @@ __global__ void density_reduce_kernel(const cx<T> *__restrict__ part, cx<T> *__r
 constexpr int kDensityGroups = 8;
 
 template <class T>
-void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *wk, cx<T> *rho,
+void density_passes(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *wk, cx<T> *rho,
+                    cx<T> *part, int nk, int nb, long long nr, int nvec, int per, dim3 grid,
+                    int ppg, int ng, long long rows1);
+
+template <class T>
+void launch_density(Context &ctx, const cx<T> *ur, const cx<T> *xr, const T *wk, cx<T> *rho,
                     cx<T> *part, int nk, int nb, long long nr, int nvec) {
+  cudaStream_t st = ctx.stream;
   // (side, k) pairs split over kDensityGroups block rows for parallelism; up to 3
   // vectors per pass (register budget), each sharing the U(r) reads
   const long long rows1 = 4LL * nk * nb;
@@ -140,10 +147,23 @@ void launch_density(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *
   const int ppg = (npair + ngroup - 1) / ngroup;
   const int ng = (npair + ppg - 1) / ppg;
   const dim3 grid(blocks_for(nr), ng);
-  // up to 3 stacked vectors per pass, each pass reading U(r) once (more vectors per
-  // pass raise the register count past two CTAs per SM and lose more than they save)
-  for (int v0 = 0; v0 < nvec; v0 += 3) {
-    const int nv = std::min(3, nvec - v0);
+  // vectors per pass (2 or 3, autotuned; 3 is the default): each pass reads U(r) once,
+  // more vectors per pass raise the register count.  Each vector's sums run in the
+  // same order whatever the grouping, so the choice changes no result.
+  char key[128];
+  snprintf(key, sizeof(key), "density/%s/nr=%lld/rows=%lld/nvec=%d",
+           sizeof(T) == 4 ? "f32" : "f64", nr, rows1, nvec);
+  ctx.tuner.pick(st, key, nvec > 1 ? std::vector<int>{2, 3} : std::vector<int>{3}, 3,
+                 [&](int per) { density_passes<T>(st, ur, xr, wk, rho, part, nk, nb, nr, nvec,
+                                                  per, grid, ppg, ng, rows1); });
+}
+
+template <class T>
+void density_passes(cudaStream_t st, const cx<T> *ur, const cx<T> *xr, const T *wk, cx<T> *rho,
+                    cx<T> *part, int nk, int nb, long long nr, int nvec, int per, dim3 grid,
+                    int ppg, int ng, long long rows1) {
+  for (int v0 = 0; v0 < nvec; v0 += per) {
+    const int nv = std::min(per, nvec - v0);
     const cx<T> *xv = xr + (long long)v0 * rows1 * nr;
     cx<T> *pv = part + (long long)v0 * 4 * nr;
     if (nv == 1)
@@ -947,7 +967,7 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
     } else {
       ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
                    (double)nbs * nr * 40.0);
-      launch_density<T>(st, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
+      launch_density<T>(ctx, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
                         w.rhopart.template as<cx<T>>(), nk, nb, nr, nvec);
     }
     if (use_h) {

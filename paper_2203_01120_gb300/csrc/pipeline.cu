@@ -15,19 +15,21 @@
 // Each pass runs the Stockham line transform of fft.cu's axis kernel on a tile
 // of TL lines held in shared memory as [position][TL + 1].
 #include <cmath>
+#include <cstdio>
 
 #include "pipeline.cuh"
 #include "regfft.cuh"
 
 // Launch KERNEL<T, N>(args) for the register-line lengths; sets ok = false otherwise.
+// (rt: threads per CTA, a variable in the calling scope)
 #define TDLZ_REG_LAUNCH(n, KERNEL, grid, ...)                                          \
   switch (n) {                                                                       \
-    case 12: KERNEL<T, 12><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 12>()); break; \
-    case 16: KERNEL<T, 16><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 16>()); break; \
-    case 24: KERNEL<T, 24><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 24>()); break; \
-    case 36: KERNEL<T, 36><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 36>()); break; \
-    case 45: KERNEL<T, 45><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 45>()); break; \
-    case 48: KERNEL<T, 48><<<grid, kRegThreads, 0, st>>>(__VA_ARGS__, regtw<T, 48>()); break; \
+    case 12: KERNEL<T, 12><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 12>()); break; \
+    case 16: KERNEL<T, 16><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 16>()); break; \
+    case 24: KERNEL<T, 24><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 24>()); break; \
+    case 36: KERNEL<T, 36><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 36>()); break; \
+    case 45: KERNEL<T, 45><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 45>()); break; \
+    case 48: KERNEL<T, 48><<<grid, rt, 0, st>>>(__VA_ARGS__, regtw<T, 48>()); break; \
     default: ok = false;                                                             \
   }
 
@@ -585,10 +587,11 @@ __global__ void __launch_bounds__(kZThreads)
 // ------------------------------------------- register-line variants (x, y axes)
 // One thread per line, the whole line in registers (regfft.cuh); neighbouring
 // threads own neighbouring lines, so each load/store of a warp is coalesced.
-constexpr int kRegThreads = 128;
+constexpr int kRegThreads = 128;   // default threads per CTA (tuned: 64, 128, 256)
+constexpr int kRegMaxThreads = 256;
 
 template <class T, int N1>
-__global__ void __launch_bounds__(kRegThreads)
+__global__ void __launch_bounds__(kRegMaxThreads)
     inv_x_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ xr,
                      const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
                      long long nr, long long rows, const RegTw<T, N1> tw) {
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(kRegThreads)
 }
 
 template <class T, int N2>
-__global__ void __launch_bounds__(kRegThreads)
+__global__ void __launch_bounds__(kRegMaxThreads)
     inv_y_reg_kernel(const cx<T> *__restrict__ i1, cx<T> *__restrict__ i2,
                      const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
                      int nsm, int npm, int n3, long long rows, const RegTw<T, N2> tw) {
@@ -674,7 +677,7 @@ __global__ void __launch_bounds__(256)
 
 // Forward X pass in registers over the products; keeps only the sphere's planes.
 template <class T, int N1>
-__global__ void __launch_bounds__(kRegThreads)
+__global__ void __launch_bounds__(kRegMaxThreads)
     fwd_x_reg_kernel(const cx<T> *__restrict__ xr, cx<T> *__restrict__ i2,
                      const int *__restrict__ plof, int nk, int nb, int npm, long long n23,
                      long long nr, long long rows, const RegTw<T, N1> tw) {
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(kRegThreads)
 }
 
 template <class T, int N2>
-__global__ void __launch_bounds__(kRegThreads)
+__global__ void __launch_bounds__(kRegMaxThreads)
     fwd_y_reg_kernel(const cx<T> *__restrict__ i2, cx<T> *__restrict__ i1,
                      const int *__restrict__ npl, const int *__restrict__ sid, int nk, int nb,
                      int nsm, int npm, int n3, long long rows, const RegTw<T, N2> tw) {
@@ -863,6 +866,18 @@ template <class T> StageWork stage_work(const QSlot &s, int nvec) {
   return w;
 }
 
+// Threads per CTA of a register-line pass (64, 128 or 256), picked by the autotuner per
+// pass and problem shape; launch(rt) enqueues the pass with rt threads per CTA.  Every
+// thread owns the same line whatever the CTA size, so the choice changes no result.
+template <class F>
+void tuned_lines(Context &ctx, const char *pass, size_t elem, int n, long long lines,
+                 long long rows, F &&launch) {
+  char key[160];
+  snprintf(key, sizeof(key), "%s/%s/n=%d/lines=%lld/rows=%lld", pass,
+           elem == 8 ? "f32" : "f64", n, lines, rows);
+  ctx.tuner.pick(ctx.stream, key, {64, 128, 256}, kRegThreads, launch);
+}
+
 template <class T>
 void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *i1, cx<T> *i2,
                       int nvec) {
@@ -898,10 +913,12 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
                wk.y_flops + wk.x_flops);
   ok = use_reg_lines<T>(n2);
   if (ok) {
-    dim3 g = grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
-    TDLZ_REG_LAUNCH(n2, inv_y_reg_kernel, g, i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk,
-                    s.nb, nsm, npm, n3, rows);
-    TDLZ_LAUNCH_CHECK();
+    tuned_lines(ctx, "inv_y", c, n2, (long long)npm * n3, rows, [&](int rt) {
+      dim3 g = grid_rows((unsigned)(((long long)npm * n3 + rt - 1) / rt), rows);
+      TDLZ_REG_LAUNCH(n2, inv_y_reg_kernel, g, i1, i2, s.pl_n.as<int>(), s.st_id.as<int>(),
+                      s.nk, s.nb, nsm, npm, n3, rows);
+      TDLZ_LAUNCH_CHECK();
+    });
   }
   if (!ok) {
     size_t sm = 2ull * n2 * (kTL + 1) * c;
@@ -913,10 +930,12 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
   }
   ok = use_reg_lines<T>(n1);
   if (ok) {
-    dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
-    TDLZ_REG_LAUNCH(n1, inv_x_reg_kernel, g, i2, xr, s.pl_of.as<int>(), s.nk, s.nb, npm, n23, s.nr,
-                    rows);
-    TDLZ_LAUNCH_CHECK();
+    tuned_lines(ctx, "inv_x", c, n1, n23, rows, [&](int rt) {
+      dim3 g = grid_rows((unsigned)((n23 + rt - 1) / rt), rows);
+      TDLZ_REG_LAUNCH(n1, inv_x_reg_kernel, g, i2, xr, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
+                      s.nr, rows);
+      TDLZ_LAUNCH_CHECK();
+    });
   }
   if (!ok) {
     size_t sm = 2ull * n1 * (kTL + 1) * c;
@@ -954,17 +973,20 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
     }
     ProfScope ps(ctx.prof, st, ST_FFT_FWD, wk.G * c + 2 * wk.S2 * c + wk.S1 * c,
                  wk.x_flops + wk.y_flops);
-    dim3 g = grid_rows((unsigned)((n23 + kRegThreads - 1) / kRegThreads), rows);
-    TDLZ_REG_LAUNCH(n1, fwd_x_reg_kernel, g, xr, i2, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
-                    s.nr, rows);
-    TDLZ_LAUNCH_CHECK();
+    tuned_lines(ctx, "fwd_x", c, n1, n23, rows, [&](int rt) {
+      dim3 g = grid_rows((unsigned)((n23 + rt - 1) / rt), rows);
+      TDLZ_REG_LAUNCH(n1, fwd_x_reg_kernel, g, xr, i2, s.pl_of.as<int>(), s.nk, s.nb, npm, n23,
+                      s.nr, rows);
+      TDLZ_LAUNCH_CHECK();
+    });
     ok = use_reg_lines<T>(n2);
     if (ok) {
-      dim3 gy =
-          grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
-      TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
-                      s.nk, s.nb, nsm, npm, n3, rows);
-      TDLZ_LAUNCH_CHECK();
+      tuned_lines(ctx, "fwd_y", c, n2, (long long)npm * n3, rows, [&](int rt) {
+        dim3 gy = grid_rows((unsigned)(((long long)npm * n3 + rt - 1) / rt), rows);
+        TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
+                        s.nk, s.nb, nsm, npm, n3, rows);
+        TDLZ_LAUNCH_CHECK();
+      });
     }
     if (!ok) {
       size_t sm = 2ull * n2 * (kTL + 1) * c;
@@ -988,11 +1010,12 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
     TDLZ_LAUNCH_CHECK();
     ok = use_reg_lines<T>(n2);
     if (ok) {
-      dim3 gy =
-          grid_rows((unsigned)(((long long)npm * n3 + kRegThreads - 1) / kRegThreads), rows);
-      TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
-                      s.nk, s.nb, nsm, npm, n3, rows);
-      TDLZ_LAUNCH_CHECK();
+      tuned_lines(ctx, "fwd_y", c, n2, (long long)npm * n3, rows, [&](int rt) {
+        dim3 gy = grid_rows((unsigned)(((long long)npm * n3 + rt - 1) / rt), rows);
+        TDLZ_REG_LAUNCH(n2, fwd_y_reg_kernel, gy, i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
+                        s.nk, s.nb, nsm, npm, n3, rows);
+        TDLZ_LAUNCH_CHECK();
+      });
     }
     if (!ok) {
       size_t smy = 2ull * n2 * (kTL + 1) * c;

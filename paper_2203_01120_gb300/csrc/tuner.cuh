@@ -1,0 +1,83 @@
+// Autotuner for launch shapes that leave the arithmetic unchanged.
+//
+// A tunable stage offers a few candidate shapes (threads per CTA of the register
+// line passes, stacked vectors per thread of the density reduction).  Every candidate
+// computes the same outputs bit for bit from the same inputs, so the choice only
+// affects time: on the first eager call with a new key (stage + problem shape) each
+// candidate runs twice, the second run timed with CUDA events on the context stream,
+// and the fastest is kept for every later call with that key (and inside captured
+// graphs).  While the stream is capturing, or with TDLZ_AUTOTUNE=0 at context
+// creation, the default candidate runs.
+#pragma once
+
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace tdlz {
+
+struct Tuner {
+  bool on = true;
+  std::map<std::string, int> choice;
+  std::map<std::string, float> best_ms;
+
+  // run(candidate) enqueues the stage on `stream`; returns the candidate used.
+  template <class F>
+  int pick(cudaStream_t stream, const std::string &key, const std::vector<int> &cands, int dflt,
+           F &&run) {
+    auto it = choice.find(key);
+    if (it != choice.end()) {
+      run(it->second);
+      return it->second;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TDLZ_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
+    if (!on || cap != cudaStreamCaptureStatusNone || cands.size() < 2) {
+      run(dflt);
+      return dflt;
+    }
+    cudaEvent_t e0, e1;
+    TDLZ_CUDA_TRY(cudaEventCreate(&e0));
+    TDLZ_CUDA_TRY(cudaEventCreate(&e1));
+    int best = dflt;
+    float tbest = -1.f;
+    for (int c : cands) {
+      run(c);  // warm-up (and the outputs, identical for every candidate)
+      TDLZ_CUDA_TRY(cudaEventRecord(e0, stream));
+      run(c);
+      TDLZ_CUDA_TRY(cudaEventRecord(e1, stream));
+      TDLZ_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      TDLZ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (tbest < 0.f || ms < tbest) {
+        tbest = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    choice[key] = best;
+    best_ms[key] = tbest;
+    return best;
+  }
+
+  // "key=choice (ms)" lines of every decision so far
+  std::string report() const {
+    std::string s;
+    for (const auto &kv : choice) {
+      char buf[64];
+      auto t = best_ms.find(kv.first);
+      snprintf(buf, sizeof(buf), "=%d (%.4f ms)\n", kv.second,
+               t == best_ms.end() ? 0.0 : (double)t->second);
+      s += kv.first + buf;
+    }
+    return s;
+  }
+};
+
+}  // namespace tdlz

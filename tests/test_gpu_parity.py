@@ -314,6 +314,35 @@ def test_larmor_mode_on_gpu(torch, ctx):
     assert np.min(np.abs(ritz - 0.1)) <= 1e-6, np.sort(np.abs(ritz - 0.1))[:3]
 
 
+@pytest.mark.parametrize("name", ["C0K", "C1"])
+def test_autotuned_shapes_change_no_result(torch, name, monkeypatch):
+    """The autotuner only picks among launch shapes that compute identical results:
+    a context with TDLZ_AUTOTUNE=0 (default shapes) and a tuning one give bitwise
+    equal L x (FP64 and mixed) and Lanczos coefficients; the tuning context reports
+    its decisions."""
+    from paper_2203_01120_gb300 import Context, TDLZ_MIXED
+    lv = liouvillian(name)
+    x = random_br_vector(lv.gs, seed=31)
+    out = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("TDLZ_AUTOTUNE", env)
+        c = Context(0)
+        try:
+            q = c.load_ground_state(ground_state(name))
+            ys = [apply_gpu(torch, c, q, x), apply_gpu(torch, c, q, x, mixed=True)]
+            chains = c.lanczos_run([q, q], [0, 2], 12, "nh", TDLZ_MIXED)
+            report = c.autotune_report()
+        finally:
+            c.close()
+        out.append((ys, chains, report))
+    (y0, c0, r0), (y1, c1, r1) = out
+    assert r0 == {} and len(r1) >= 1, r1
+    for a, b in zip(y0, y1):
+        assert np.array_equal(a, b)
+    for key in ("alpha", "beta", "gamma", "z"):
+        assert np.array_equal(c0[key], c1[key]), key
+
+
 def test_restart_rejects_mismatched_image(torch, ctx):
     from paper_2203_01120_gb300 import TdlzError
     q = slot(ctx, "C1")
