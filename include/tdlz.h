@@ -267,7 +267,8 @@ int64_t tdlz_launch_count(void);
 /* Autotuner decisions of this context so far, one "stage/shape=choice (ms)" line per
  * tuned stage and shape (threads per CTA of the register-line FFT passes, vectors per
  * density pass).  Every candidate computes identical results; the first eager call
- * with a new shape times each candidate on the context stream and keeps the fastest.
+ * with a new shape times each candidate on the context stream and keeps the fastest
+ * (decisions are shared by the contexts of a process on the same device).
  * TDLZ_AUTOTUNE=0 in the environment at tdlz_create keeps the defaults.  Writes at most
  * len bytes including the terminating NUL into the caller's host buffer buf and the
  * full length (without NUL) into *needed (may be NULL).  Host-only, no launch. */

@@ -80,6 +80,7 @@ tdlz_status tdlz_create(tdlz_ctx **out, int device, void *cuda_stream) {
   // TDLZ_AUTOTUNE=0 keeps every tunable stage at its default launch shape
   const char *at = std::getenv("TDLZ_AUTOTUNE");
   ctx->c.tuner.on = !(at && at[0] == '0');
+  ctx->c.tuner.device = device;
   if (cuda_stream) {
     ctx->c.stream = (cudaStream_t)cuda_stream;
   } else {

@@ -4,14 +4,15 @@
 // line passes, stacked vectors per thread of the density reduction).  Every candidate
 // computes the same outputs bit for bit from the same inputs, so the choice only
 // affects time: on the first eager call with a new key (stage + problem shape) each
-// candidate runs twice, the second run timed with CUDA events on the context stream,
-// and the fastest is kept for every later call with that key (and inside captured
-// graphs).  While the stream is capturing, or with TDLZ_AUTOTUNE=0 at context
-// creation, the default candidate runs.
+// candidate runs once, timed with CUDA events on the context stream, and the fastest
+// is kept for every later call with that key (and inside captured graphs).  Decisions
+// are shared by the contexts of a process on the same device.  While the stream is
+// capturing, or with TDLZ_AUTOTUNE=0 at context creation, the default candidate runs.
 #pragma once
 
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,8 +22,24 @@
 
 namespace tdlz {
 
+struct TunedShape {
+  int choice;
+  float ms;
+};
+
+// decisions of every context of the process, keyed by device and stage/shape
+inline std::map<std::string, TunedShape> &tuner_shared() {
+  static std::map<std::string, TunedShape> m;
+  return m;
+}
+inline std::mutex &tuner_mutex() {
+  static std::mutex m;
+  return m;
+}
+
 struct Tuner {
   bool on = true;
+  int device = 0;
   std::map<std::string, int> choice;
   std::map<std::string, float> best_ms;
 
@@ -41,13 +58,23 @@ struct Tuner {
       run(dflt);
       return dflt;
     }
+    const std::string gkey = std::to_string(device) + ":" + key;
+    {
+      std::lock_guard<std::mutex> lk(tuner_mutex());
+      auto g = tuner_shared().find(gkey);
+      if (g != tuner_shared().end()) {
+        choice[key] = g->second.choice;
+        best_ms[key] = g->second.ms;
+        run(g->second.choice);
+        return g->second.choice;
+      }
+    }
     cudaEvent_t e0, e1;
     TDLZ_CUDA_TRY(cudaEventCreate(&e0));
     TDLZ_CUDA_TRY(cudaEventCreate(&e1));
     int best = dflt;
     float tbest = -1.f;
-    for (int c : cands) {
-      run(c);  // warm-up (and the outputs, identical for every candidate)
+    for (int c : cands) {  // each run also leaves the outputs, identical for every candidate
       TDLZ_CUDA_TRY(cudaEventRecord(e0, stream));
       run(c);
       TDLZ_CUDA_TRY(cudaEventRecord(e1, stream));
@@ -63,6 +90,10 @@ struct Tuner {
     cudaEventDestroy(e1);
     choice[key] = best;
     best_ms[key] = tbest;
+    {
+      std::lock_guard<std::mutex> lk(tuner_mutex());
+      tuner_shared().emplace(gkey, TunedShape{best, tbest});
+    }
     return best;
   }
 
