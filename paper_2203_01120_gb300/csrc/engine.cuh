@@ -116,6 +116,8 @@ struct QSlot {
   int nstick_max = 0, nplane_max = 0;
   DevBuf st_n;    // [nk] sticks per k
   DevBuf st_map;  // [nk][nstick_max][n3] sphere index of (stick, j3) or -1
+  DevBuf st_run;  // [nk][nstick_max + 1] int4 (first plane wave, run A length, run A j3, run B j3)
+  bool st_runs = false;  // every stick is at most two j3 runs (st_run valid)
   DevBuf pl_n;    // [nk] planes per k
   DevBuf pl_j1;   // [nk][nplane_max] grid index j1 of each plane
   DevBuf pl_of;   // [nk][n1] plane index of j1 or -1

@@ -14,6 +14,7 @@
 //   Z: writing only sphere coefficients, fused with + (|k+q+G|^2/2 - e_n) x.
 // Each pass runs the Stockham line transform of fft.cu's axis kernel on a tile
 // of TL lines held in shared memory as [position][TL + 1].
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -469,28 +470,64 @@ template <class T, int N1, int N2, bool TR>
 __global__ void __launch_bounds__(kZThreads)
     inv_z_reg_kernel(const cx<T> *__restrict__ x, cx<T> *__restrict__ i1,
                      const int *__restrict__ nst, const int *__restrict__ smap, int nk, int nb,
-                     int npwx, int nsm, T scale, long long rows, const RegTw<T, N2> tw2,
-                     const RegTw<T, N1 * N2> twn) {
+                     int npwx, int nsm, T scale, long long rows, const int4 *__restrict__ runs,
+                     const RegTw<T, N2> tw2, const RegTw<T, N1 * N2> twn) {
   constexpr int N = N1 * N2, LPB = kZThreads / N1;
   const long long row = row_of_block();
   if (row >= rows) return;
   const int k = (int)((row / (2 * nb)) % nk);
   const int line = blockIdx.x * LPB + threadIdx.x / N1, n1 = threadIdx.x % N1;
   const bool valid = line < __ldg(nst + k);
-  const int *mp = smap + ((long long)k * nsm + (valid ? line : 0)) * N;
   const cx<T> *xrow = x + row * npwx;
   cx<T> a[N2];
+  bool filled = false;
+  cx<T> *ws = nullptr;
+  if constexpr (ZStage<T, N1, N2, TR>::on) {
+    using Z = ZStage<T, N1, N2, TR>;
+    __shared__ cx<T> zs[kZThreads / 32][Z::LW * Z::S];
+    __shared__ int4 zd[kZThreads / 32][Z::LW + 1];
+    ws = zs[threadIdx.x >> 5];
+    if (runs) {
+      // the warp's sticks are consecutive, so their plane waves are one contiguous run
+      // of x: read it coalesced into the lines' natural j3 slots (zeros elsewhere)
+      const int lane = threadIdx.x & 31, ll = lane / N1;
+      const int l0 = blockIdx.x * LPB + (threadIdx.x >> 5) * Z::LW;
+      const int nv = min(max(__ldg(nst + k) - l0, 0), Z::LW);
+      int4 *wd = zd[threadIdx.x >> 5];
+      if (lane <= nv) wd[lane] = __ldg(runs + (long long)k * (nsm + 1) + l0 + lane);
+      for (int e = lane; e < Z::LW * Z::S; e += 32) ws[e] = czero<T>();
+      __syncwarp();
+      if (nv > 0) {
+        const int g1 = wd[nv].x;
+        for (int e = wd[0].x + lane; e < g1; e += 32) {
+          int l = 0;
 #pragma unroll
-  for (int j = 0; j < N2; ++j) {
-    const int g = valid ? __ldg(mp + n1 + N1 * j) : -1;
-    a[j] = g >= 0 ? cscale<T>(xrow[g], scale) : czero<T>();
+          for (int t = 1; t < Z::LW; ++t) l += (t < nv && e >= wd[t].x) ? 1 : 0;
+          const int4 d = wd[l];
+          const int rho = e - d.x;
+          const int z = rho < d.y ? d.z + rho : d.w + (rho - d.y);
+          if ((unsigned)z < (unsigned)N) ws[l * Z::S + z] = cscale<T>(xrow[e], scale);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < N2; ++j) a[j] = ws[ll * Z::S + n1 + N1 * j];
+      __syncwarp();
+      filled = true;
+    }
+  }
+  if (!filled) {
+    const int *mp = smap + ((long long)k * nsm + (valid ? line : 0)) * N;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) {
+      const int g = valid ? __ldg(mp + n1 + N1 * j) : -1;
+      a[j] = g >= 0 ? cscale<T>(xrow[g], scale) : czero<T>();
+    }
   }
   const int k1 = zline_fft<T, N1, N2, +1>(a, n1, tw2, twn);
   if constexpr (ZStage<T, N1, N2, TR>::on) {
     // the warp's lines through shared memory, then one contiguous block per warp
     using Z = ZStage<T, N1, N2, TR>;
-    __shared__ cx<T> zs[kZThreads / 32][Z::LW * Z::S];
-    cx<T> *ws = zs[threadIdx.x >> 5];
     const int ll = (threadIdx.x & 31) / N1, lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < N2; ++j) ws[ll * Z::S + k1 * (N2 + 1) + j] = a[j];
@@ -524,7 +561,8 @@ __global__ void __launch_bounds__(kZThreads)
                      cx<T> *__restrict__ h, const int *__restrict__ nst,
                      const int *__restrict__ smap, const T *__restrict__ kin,
                      const T *__restrict__ evals, int nk, int nb, int npwx, int nsm, T scale,
-                     long long rows, const RegTw<T, N2> tw2, const RegTw<T, N1 * N2> twn) {
+                     long long rows, const int4 *__restrict__ runs, const RegTw<T, N2> tw2,
+                     const RegTw<T, N1 * N2> twn) {
   constexpr int N = N1 * N2, LPB = kZThreads / N1;
   const long long row = row_of_block();
   if (row >= rows) return;
@@ -548,14 +586,40 @@ __global__ void __launch_bounds__(kZThreads)
   const cx<T> *xrow = x + row * npwx;
   cx<T> *hrow = h + row * npwx;
   if constexpr (ZStage<T, N1, N2, TR>::on) {
-    // transpose through shared memory so that lane n1 holds X[n1 + N1 j]: the four lanes
-    // of a line then scatter to consecutive plane waves of the stick (j3 ascending)
     using Z = ZStage<T, N1, N2, TR>;
     __shared__ cx<T> zs[kZThreads / 32][Z::LW * Z::S];
+    __shared__ int4 zd[kZThreads / 32][Z::LW + 1];
     cx<T> *ws = zs[threadIdx.x >> 5];
-    const int ll = (threadIdx.x & 31) / N1;
+    const int ll = (threadIdx.x & 31) / N1, lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < N2; ++j) ws[ll * Z::S + k1 * (N2 + 1) + j] = a[j];
+    if (runs) {
+      // the warp's sticks are one contiguous run of plane waves: write it coalesced,
+      // each plane wave reading its line's transform at its j3
+      const int l0 = blockIdx.x * LPB + (threadIdx.x >> 5) * Z::LW;
+      const int nv = min(max(__ldg(nst + k) - l0, 0), Z::LW);
+      int4 *wd = zd[threadIdx.x >> 5];
+      if (lane <= nv) wd[lane] = __ldg(runs + (long long)k * (nsm + 1) + l0 + lane);
+      __syncwarp();
+      if (nv == 0) return;
+      const int g1 = wd[nv].x;
+      for (int e = wd[0].x + lane; e < g1; e += 32) {
+        int l = 0;
+#pragma unroll
+        for (int t = 1; t < Z::LW; ++t) l += (t < nv && e >= wd[t].x) ? 1 : 0;
+        const int4 d = wd[l];
+        const int rho = e - d.x;
+        const int z = min(max(rho < d.y ? d.z + rho : d.w + (rho - d.y), 0), N - 1);
+        const int q = z / N2;
+        const cx<T> v = ws[l * Z::S + q * (N2 + 1) + (z - q * N2)];
+        const cx<T> xv = xrow[e];
+        const T dd = kk[e] - e_n;
+        hrow[e] = mk<T>(v.x * scale + dd * xv.x, v.y * scale + dd * xv.y);
+      }
+      return;
+    }
+    // otherwise transpose through shared memory so that lane n1 holds X[n1 + N1 j]: the
+    // four lanes of a line then scatter to consecutive plane waves of the stick
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < N2; ++j)
@@ -833,10 +897,51 @@ void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
         sid[((size_t)k * npm + p) * n2 + j2] = stick_of_cell[k][j1 * n2 + j2];
     }
   }
+  // Sticks as runs of the stick-major plane-wave order: run[k][st] = (first plane wave,
+  // length of the first j3 run, its first j3, first j3 of the second run), run[k][nst] =
+  // (npw, 0, 0, 0).  Needs every stick's j3 values to form at most two runs (true for a
+  // sphere: one interval of Miller m3, split in two where it wraps); otherwise the Z
+  // passes keep the per-point map.
+  std::vector<int> run((size_t)nk * (nsm + 1) * 4, 0);
+  bool runs_ok = true;
+  for (int k = 0; k < nk && runs_ok; ++k) {
+    const int *id = idx_kq.data() + (size_t)k * npwx;
+    int st = -1, prev_c = -1, prev_z = -1, nrun = 0;
+    for (int g = 0; g < s.npw_kq[k]; ++g) {
+      const int c = id[g] / n3, z = id[g] % n3;
+      int *r = nullptr;
+      if (c != prev_c) {  // a new stick (cells ascend in the stick-major order)
+        ++st;
+        if (stick_of_cell[k][c] != st) { runs_ok = false; break; }
+        r = run.data() + ((size_t)k * (nsm + 1) + st) * 4;
+        r[0] = g; r[1] = 1; r[2] = z; r[3] = 0;
+        nrun = 1;
+      } else {
+        r = run.data() + ((size_t)k * (nsm + 1) + st) * 4;
+        if (z <= prev_z) { runs_ok = false; break; }
+        if (z == prev_z + 1) {
+          if (nrun == 1) ++r[1];
+        } else if (nrun == 1) {
+          r[3] = z;
+          nrun = 2;
+        } else {
+          runs_ok = false;
+          break;
+        }
+      }
+      prev_c = c;
+      prev_z = z;
+    }
+    if (st + 1 != nst[k]) runs_ok = false;
+    int *end = run.data() + ((size_t)k * (nsm + 1) + nst[k]) * 4;
+    end[0] = s.npw_kq[k];
+  }
+  s.st_runs = runs_ok;
   auto up = [&](DevBuf &b, const std::vector<int> &v) {
     b.alloc(v.size() * sizeof(int));
     TDLZ_CUDA_TRY(cudaMemcpy(b.p, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
   };
+  up(s.st_run, run);
   up(s.st_n, nst);
   up(s.st_map, smap);
   up(s.pl_n, npl);
@@ -864,6 +969,31 @@ template <class T> StageWork stage_work(const QSlot &s, int nvec) {
   w.y_flops = rows * s.nplane_max * n3 * 5.0 * n2 * std::log2((double)n2);
   w.x_flops = rows * (double)n2 * n3 * 5.0 * n1 * std::log2((double)n1);
   return w;
+}
+
+// h[row][i] = 0 for npw_kq[k] <= i < npwx: the sphere scatter writes every sphere point
+// exactly once (each point is one (stick, j3) of its k+q sphere), so only the padding
+// needs clearing before it.
+template <class T>
+__global__ void zero_padding_kernel(cx<T> *__restrict__ h, const int *__restrict__ npw, int nk,
+                                    int nb, int npwx, long long rows) {
+  const long long row = row_of_block();
+  if (row >= rows) return;
+  const int k = (int)((row / (2 * nb)) % nk);
+  for (int i = __ldg(npw + k) + blockIdx.x * blockDim.x + threadIdx.x; i < npwx;
+       i += gridDim.x * blockDim.x)
+    h[row * npwx + i] = czero<T>();
+}
+
+template <class T>
+void zero_padding(Context &ctx, QSlot &s, cx<T> *h, long long rows) {
+  int npw_min = s.npwx;
+  for (int v : s.npw_kq) npw_min = std::min(npw_min, v);
+  const int pad = s.npwx - npw_min;
+  if (pad <= 0) return;
+  zero_padding_kernel<T><<<grid_rows((unsigned)((pad + 255) / 256), rows), 256, 0, ctx.stream>>>(
+      h, s.npwkq_d.as<int>(), s.nk, s.nb, s.npwx, rows);
+  TDLZ_LAUNCH_CHECK();
 }
 
 // Threads per CTA of a register-line pass (64, 128 or 256), picked by the autotuner per
@@ -897,7 +1027,7 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
       dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
       TDLZ_Z_LAUNCH(zn1, zn2, inv_z_reg_kernel, false, g, x, i1, s.st_n.as<int>(),
                     s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, (T)(1.0 / std::sqrt(s.omega)),
-                    rows);
+                    rows, s.st_runs ? s.st_run.as<int4>() : (const int4 *)nullptr);
     }
     if (!ok) {
       size_t sm = 2ull * n3 * (kTL + 1) * c;
@@ -1027,9 +1157,9 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
     }
   }
   {
-    // sticks in; x read, h zeroed and written on the sphere
+    // sticks in; x read, h written on the sphere and zero on the padding
     ProfScope ps(ctx.prof, st, ST_GATHER, wk.S1 * c + 3 * wk.V * c, wk.z_flops);
-    TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * c, st));
+    zero_padding<T>(ctx, s, h, rows);
     int zn1, zn2;
     z_plan(n3, zn1, zn2);
     ok = false;
@@ -1038,7 +1168,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
       dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
       TDLZ_Z_LAUNCH(zn1, zn2, fwd_z_reg_kernel, false, g, i1, x, h, s.st_n.as<int>(),
                     s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
-                    (T)(std::sqrt(s.omega) / s.nr), rows);
+                    (T)(std::sqrt(s.omega) / s.nr), rows, s.st_runs ? s.st_run.as<int4>() : (const int4 *)nullptr);
     }
     if (!ok) {
       size_t sm = 2ull * n3 * (kTL + 1) * c;
@@ -1067,7 +1197,7 @@ void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec
     dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
     TDLZ_Z_LAUNCH(zn1, zn2, inv_z_reg_kernel, true, g, x, i1t, s.st_n.as<int>(),
                   s.st_map.as<int>(), s.nk, s.nb, s.npwx, nsm, (T)(1.0 / std::sqrt(s.omega)),
-                  rows);
+                  rows, (const int4 *)nullptr);
   }
   if (!ok) {
     size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
@@ -1086,7 +1216,7 @@ void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, co
   const int n3 = s.fft[2];
   const long long rows = s.rows() * nvec;
   const int nsm = s.nstick_max;
-  TDLZ_CUDA_TRY(cudaMemsetAsync(h, 0, (size_t)s.br_elems() * nvec * sizeof(cx<T>), st));
+  zero_padding<T>(ctx, s, h, rows);
   int zn1, zn2;
   z_plan(n3, zn1, zn2);
   bool ok = false;
@@ -1095,7 +1225,7 @@ void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, co
     dim3 g = grid_rows((unsigned)((nsm + lpb - 1) / lpb), rows);
     TDLZ_Z_LAUNCH(zn1, zn2, fwd_z_reg_kernel, true, g, i1t, x, h, s.st_n.as<int>(),
                   s.st_map.as<int>(), kin, evals, s.nk, s.nb, s.npwx, nsm,
-                  (T)(std::sqrt(s.omega) / s.nr), rows);
+                  (T)(std::sqrt(s.omega) / s.nr), rows, (const int4 *)nullptr);
   }
   if (!ok) {
     size_t sm = 2ull * n3 * (kTL + 1) * sizeof(cx<T>);
