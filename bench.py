@@ -247,6 +247,24 @@ def run_reference(args):
 NCU_TRAFFIC = {("C2", "product"): 4 * 8.845e9}
 
 
+# GB300's FP64 vector rate (nominal, dense): the binding roof of the FP64 path, whose
+# FFT, pointwise and GEMM stages all run on the FP64 pipe.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_roofline(prof64):
+    """Nominal flops of the profiled FP64 steps (per stage: 5 N log2 N per line transform,
+    8 per complex multiply-add of the contractions, the pointwise products) over their
+    CUDA-event time, against the FP64 rate."""
+    ms = sum(v["ms"] for v in prof64.values())
+    fl = sum(v["flops"] for v in prof64.values())
+    if ms <= 0:
+        return None
+    achieved = fl / (ms / 1000) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}
+
+
 def ncu_traffic(args, stage):
     if args.kpoints or args.flavor != "nh" or args.chains != 3:
         return None
@@ -376,7 +394,8 @@ def run_tdlz(args):
                    "l2": "inputs larger than L2 (per-step working set > 5 GB)"},
         "fp64": None if sps_fp64 is None else {
             "value": sps_fp64, "unit": "steps/s", "steps": fp64_steps,
-            "ms_per_step": 1000 * wall_fp64 / fp64_steps},
+            "ms_per_step": 1000 * wall_fp64 / fp64_steps,
+            "roofline": fp64_roofline(prof64)},
         "chi_rel_err": chi_err, "chi_steps": m, "chi_tolerance": 1e-4,
         "roofline": {"bound": "hbm", "stage": top, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,

@@ -371,6 +371,95 @@ __global__ void __launch_bounds__(kRedThreads)
   block_sum_store<4>(acc, partial);
 }
 
+// NH, the M <= 4 chains of one group at once: partial[c][blk][0..3] = (p~_c^H J a_c,
+// q_c^H u^0, q_c^H u^1, q_c^H u^2), each u^l read once for every chain of the group.
+struct NhGroupDots {
+  const void *p[4], *a[4], *q[4];
+  const void *u[3];
+};
+constexpr int kGroupUnroll = 2;
+template <class T, int M>
+__global__ void __launch_bounds__(kRedThreads)
+    nh_group_dots_kernel(NhGroupDots g, long long n, long long half, double2 *partial) {
+  double2 acc[M][4];
+#pragma unroll
+  for (int c = 0; c < M; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[c][i] = make_double2(0.0, 0.0);
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  const long long bd = blockDim.x;
+  const cx<T> *U[3] = {reinterpret_cast<const cx<T> *>(g.u[0]),
+                       reinterpret_cast<const cx<T> *>(g.u[1]),
+                       reinterpret_cast<const cx<T> *>(g.u[2])};
+  long long e = b0 + threadIdx.x;
+  while (e < b1) {
+    T rx[M][4], ry[M][4];
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) rx[c][i] = ry[c][i] = T(0);
+    for (int it = 0; it < kRun / kGroupUnroll && e < b1; ++it) {
+      cx<T> uv[kGroupUnroll][3], pv[kGroupUnroll][M], av[kGroupUnroll][M], qv[kGroupUnroll][M];
+#pragma unroll
+      for (int w = 0; w < kGroupUnroll; ++w) {
+        const long long ew = e + w * bd;
+        const bool in = ew < b1;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) uv[w][l] = in ? U[l][ew] : czero<T>();
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          pv[w][c] = in ? reinterpret_cast<const cx<T> *>(g.p[c])[ew] : czero<T>();
+          av[w][c] = in ? reinterpret_cast<const cx<T> *>(g.a[c])[ew] : czero<T>();
+          qv[w][c] = in ? reinterpret_cast<const cx<T> *>(g.q[c])[ew] : czero<T>();
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < kGroupUnroll; ++w) {
+        const T sg = e + w * bd >= half ? T(-1) : T(1);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          rx[c][0] += sg * (pv[w][c].x * av[w][c].x + pv[w][c].y * av[w][c].y);
+          ry[c][0] += sg * (pv[w][c].x * av[w][c].y - pv[w][c].y * av[w][c].x);
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            rx[c][1 + l] += qv[w][c].x * uv[w][l].x + qv[w][c].y * uv[w][l].y;
+            ry[c][1 + l] += qv[w][c].x * uv[w][l].y - qv[w][c].y * uv[w][l].x;
+          }
+        }
+      }
+      e += kGroupUnroll * bd;
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[c][i].x += (double)rx[c][i];
+        acc[c][i].y += (double)ry[c][i];
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) block_sum_store<4>(acc[c], partial + (long long)c * gridDim.x * 4);
+}
+
+// x_v *= *s_v for the nv vectors of a set (the new Lanczos vectors of a group)
+struct ScaleSet {
+  void *x[32];
+  const double2 *s[32];
+};
+template <class T>
+__global__ void scale_set_kernel(ScaleSet ss, long long n) {
+  const int v = blockIdx.y;
+  cx<T> *x = reinterpret_cast<cx<T> *>(ss.x[v]);
+  const double2 sc = *ss.s[v];
+  const T sr = (T)sc.x, si = (T)sc.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cx<T> a = x[i];
+    x[i] = mk<T>(a.x * sr - a.y * si, a.x * si + a.y * sr);
+  }
+}
+
 template <class T>
 __global__ void jflip_kernel(const cx<T> *x, cx<T> *y, long long n, long long half) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -412,7 +501,7 @@ template void jflip_copy<float>(Context &, QSlot &, const float2 *, float2 *);
 template <class T>
 void ChainSet::init_impl() {
   const size_t c = sizeof(cx<T>);
-  red.alloc((size_t)kRedBlocks * 4 * sizeof(double2));
+  red.alloc((size_t)kRedBlocks * 4 * 16 * sizeof(double2));  // up to 16 chains per group
   for (size_t i = 0; i < chains.size(); ++i) {
     Chain &ch = chains[i];
     int g = -1;
@@ -494,6 +583,55 @@ void ChainSet::advance_impl(int nsteps) {
       if (flavor == TDLZ_NONHERMITIAN) {
         // a = L q and b~ = L p~ = J L^H p for every member in one pass
         apply_liouvillian<T>(*ctx, s, S0, S2, 2 * m, 0u);
+        if (m <= 4) {
+          // the group's dots in one pass (u^l read once), then per chain the scalars and
+          // the update, then every new vector rescaled in one launch
+          ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, (15.0 * m + 3.0) * n * sizeof(cx<T>),
+                       40.0 * m * n);
+          NhGroupDots gd{};
+          for (int mi = 0; mi < m; ++mi) {
+            gd.q[mi] = S0 + mi * n;
+            gd.p[mi] = S0 + (m + mi) * n;
+            gd.a[mi] = S2 + mi * n;
+          }
+          for (int l = 0; l < 3; ++l) gd.u[l] = u + l * n;
+          switch (m) {
+            case 1: nh_group_dots_kernel<T, 1><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
+            case 2: nh_group_dots_kernel<T, 2><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
+            case 3: nh_group_dots_kernel<T, 3><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
+            default: nh_group_dots_kernel<T, 4><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
+          }
+          TDLZ_LAUNCH_CHECK();
+          const long long pstride = (long long)kRedBlocks * 4;
+          for (int mi = 0; mi < m; ++mi) {
+            Chain &ch = chains[gr.members[mi]];
+            scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(
+                part + mi * pstride, kRedBlocks, ch.sc.as<ChainScalars>(), ch.cf, flavor);
+            TDLZ_LAUNCH_CHECK();
+          }
+          ScaleSet ss{};
+          for (int mi = 0; mi < m; ++mi) {
+            Chain &ch = chains[gr.members[mi]];
+            ChainScalars *cs = ch.sc.as<ChainScalars>();
+            cx<T> *Q = S0 + mi * n, *P = S0 + (m + mi) * n, *QP = S1 + mi * n,
+                  *PP = S1 + (m + mi) * n, *A = S2 + mi * n, *B = S2 + (m + mi) * n;
+            double2 *pc = part + mi * pstride;
+            update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(A, Q, QP, B, P, PP, cs,
+                                                                         flavor, n, half, pc);
+            TDLZ_LAUNCH_CHECK();
+            scalar_b_kernel<<<1, kRedThreads, 0, ctx->stream>>>(pc, kRedBlocks, cs, ch.cf, flavor);
+            TDLZ_LAUNCH_CHECK();
+            ss.x[mi] = QP;
+            ss.s[mi] = &cs->scale_q;
+            ss.x[m + mi] = PP;
+            ss.s[m + mi] = &cs->scale_p;
+          }
+          scale_set_kernel<T><<<dim3(blocks_for(n) / 2 + 1, 2 * m), 256, 0, ctx->stream>>>(ss, n);
+          TDLZ_LAUNCH_CHECK();
+          std::swap(gr.slot[0], gr.slot[1]);
+          gr.host_step++;
+          continue;
+        }
         ProfScope ps(ctx->prof, ctx->stream, ST_LANCZOS, 18.0 * m * n * sizeof(cx<T>),
                      40.0 * m * n);
         for (int mi = 0; mi < m; ++mi) {

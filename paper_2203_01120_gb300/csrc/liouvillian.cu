@@ -71,48 +71,111 @@ __global__ void __launch_bounds__(256)
   const long long rows1 = 4LL * nk * nb;
   const int pb = blockIdx.y * ppg, pe = min(2 * nk, pb + ppg);
   rho += (long long)blockIdx.y * vstride * 4 * nr;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
-       r += (long long)gridDim.x * blockDim.x) {
-    cx<T> acc[NV][4];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[v][a] = czero<T>();
-    for (int pair = pb; pair < pe; ++pair) {
-      const int side = pair / nk, k = pair - side * nk;
-      const T w = wk[k], wt = side == 0 ? w : -w;
-      cx<T> a[NV][4];
+  if constexpr (sizeof(T) == 4) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+         r += (long long)gridDim.x * blockDim.x) {
+      // acc[v][a] = sum over the group's (side, k) pairs and bands of w t_a U^+ s_a x, with
+      // t = (1, -1, -1, -1) on the Y side: U is scaled once per band by w t_1 (= +-w), and
+      // the charge part (t_0 = 1) takes the same products with the side's sign, so no
+      // per-pair partial sums are needed
+      cx<T> acc[NV][4];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) a[v][c] = czero<T>();
-      for (int n = 0; n < nb; ++n) {
+        for (int a = 0; a < 4; ++a) acc[v][a] = czero<T>();
+      const int nit = (pe - pb) * nb;
+      // loads of iteration it + 1 issued before the products of iteration it
+      auto load = [&](int it, cx<T> &u0, cx<T> &u1, cx<T> (&x)[NV][2]) {
+        const int pair = pb + it / nb, n = it - (it / nb) * nb;
         const long long row = ((long long)pair * nb + n) * 2;
-        const cx<T> u0 = __ldg(ur + row * nr + r), u1 = __ldg(ur + (row + 1) * nr + r);
+        u0 = __ldg(ur + row * nr + r);
+        u1 = __ldg(ur + (row + 1) * nr + r);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {  // every vector of the pass: no early exit, so
-          const long long rv = row + v * rows1;  // all loads of a band issue together
-          const cx<T> x0 = xr[rv * nr + r], x1 = xr[(rv + 1) * nr + r];
-          const cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
-          const cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
-          a[v][0] = cadd<T>(a[v][0], cadd<T>(p00, p11));
-          a[v][1] = cadd<T>(a[v][1], cadd<T>(p01, p10));
+        for (int v = 0; v < NV; ++v) {
+          const long long rv = row + v * rows1;
+          x[v][0] = xr[rv * nr + r];
+          x[v][1] = xr[(rv + 1) * nr + r];
+        }
+      };
+      cx<T> u0, u1, xv[NV][2];
+      if (nit > 0) load(0, u0, u1, xv);
+      for (int it = 0; it < nit; ++it) {
+        const cx<T> cu0 = u0, cu1 = u1;
+        cx<T> cx_[NV][2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          cx_[v][0] = xv[v][0];
+          cx_[v][1] = xv[v][1];
+        }
+        if (it + 1 < nit) load(it + 1, u0, u1, xv);
+        const int pair = pb + it / nb;
+        const int side = pair / nk, k = pair - side * nk;
+        const T w = wk[k], wt = side == 0 ? w : -w;
+        const cx<T> b0 = cscale<T>(cu0, wt), b1 = cscale<T>(cu1, wt);   // magnetic weight
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {  // every vector of the pass: no early exit
+          const cx<T> x0 = cx_[v][0], x1 = cx_[v][1];
+          const cx<T> p00 = cmulc<T>(b0, x0), p01 = cmulc<T>(b0, x1);
+          const cx<T> p10 = cmulc<T>(b1, x0), p11 = cmulc<T>(b1, x1);
+          const cx<T> c = cadd<T>(p00, p11);  // charge: w (U^+ x), i.e. +-(b^+ x)
+          acc[v][0] = side == 0 ? cadd<T>(acc[v][0], c) : csub<T>(acc[v][0], c);
+          acc[v][1] = cadd<T>(acc[v][1], cadd<T>(p01, p10));
           const cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
-          a[v][2] = cadd<T>(a[v][2], mk<T>(-d.y, d.x));
-          a[v][3] = cadd<T>(a[v][3], csub<T>(p00, p11));
+          acc[v][2] = cadd<T>(acc[v][2], mk<T>(-d.y, d.x));
+          acc[v][3] = cadd<T>(acc[v][3], csub<T>(p00, p11));
         }
       }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        acc[v][0] = cadd<T>(acc[v][0], cscale<T>(a[v][0], w));
+      for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int c = 1; c < 4; ++c) acc[v][c] = cadd<T>(acc[v][c], cscale<T>(a[v][c], wt));
-      }
+        for (int a = 0; a < 4; ++a) rho[((long long)v * 4 + a) * nr + r] = acc[v][a];
     }
+  } else {
+    // FP64 (bound by the FP64 rate): products shared by the charge and magnetic parts,
+    // the k weights applied once per (side, k) pair
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr;
+         r += (long long)gridDim.x * blockDim.x) {
+      cx<T> acc[NV][4];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
+      for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int a = 0; a < 4; ++a) rho[((long long)v * 4 + a) * nr + r] = acc[v][a];
+        for (int a = 0; a < 4; ++a) acc[v][a] = czero<T>();
+      for (int pair = pb; pair < pe; ++pair) {
+        const int side = pair / nk, k = pair - side * nk;
+        const T w = wk[k], wt = side == 0 ? w : -w;
+        cx<T> a[NV][4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a[v][c] = czero<T>();
+        for (int n = 0; n < nb; ++n) {
+          const long long row = ((long long)pair * nb + n) * 2;
+          const cx<T> u0 = __ldg(ur + row * nr + r), u1 = __ldg(ur + (row + 1) * nr + r);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {  // every vector of the pass: no early exit, so
+            const long long rv = row + v * rows1;  // all loads of a band issue together
+            const cx<T> x0 = xr[rv * nr + r], x1 = xr[(rv + 1) * nr + r];
+            const cx<T> p00 = cmulc<T>(u0, x0), p01 = cmulc<T>(u0, x1);
+            const cx<T> p10 = cmulc<T>(u1, x0), p11 = cmulc<T>(u1, x1);
+            a[v][0] = cadd<T>(a[v][0], cadd<T>(p00, p11));
+            a[v][1] = cadd<T>(a[v][1], cadd<T>(p01, p10));
+            const cx<T> d = csub<T>(p10, p01);  // m_y: i (p10 - p01)
+            a[v][2] = cadd<T>(a[v][2], mk<T>(-d.y, d.x));
+            a[v][3] = cadd<T>(a[v][3], csub<T>(p00, p11));
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          acc[v][0] = cadd<T>(acc[v][0], cscale<T>(a[v][0], w));
+#pragma unroll
+          for (int c = 1; c < 4; ++c) acc[v][c] = cadd<T>(acc[v][c], cscale<T>(a[v][c], wt));
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) rho[((long long)v * 4 + a) * nr + r] = acc[v][a];
+    }
   }
 }
 
