@@ -244,7 +244,7 @@ def run_reference(args):
 # (dram__bytes_read.sum + dram__bytes_write.sum): the product kernel of the C2 step
 # (6 stacked vectors) captured at 4 of the 16 k points, scaled by 4 (its traffic is
 # linear in the number of k points).  Summary: profiles/kernels_C2_k4_full.md.
-NCU_TRAFFIC = {("C2", "product"): 4 * 8.845e9}
+NCU_TRAFFIC = {("C2", "product"): 4 * 8.837e9}
 
 
 # GB300's FP64 vector rate (nominal, dense): the binding roof of the FP64 path, whose
