@@ -39,6 +39,16 @@ WORKLOAD = ("C2: hexagonal a=13 c=30 bohr, FFT 36x36x96, ~5000 PW/component, 4x4
             "Nocc=40, 8 atoms x 8 KB projectors with SOC, q=(1/8,0,0) 2pi/a")
 
 
+def workload(name):
+    """The workload label of the JSON line: the C2 description, or the config's own shape."""
+    if name == "C2":
+        return WORKLOAD
+    from synth.configs import CONFIGS
+    c = CONFIGS[name]
+    return (f"{name}: {c.kind} cell, FFT {'x'.join(map(str, c.fft))}, ecut {c.ecut} Ha, "
+            f"{c.kgrid[0]}x{c.kgrid[1]}x{c.kgrid[2]} k, Nocc={c.nocc}, q={tuple(c.q_2pi_a)} 2pi/a")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,7 +239,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "flavor": args.flavor},
+        "config": {"workload": workload(args.config), "flavor": args.flavor},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                          "sample": "each step: one oracle Lanczos step restricted to k point 0 "
                                    f"of {gs.nk}, time x {gs.nk} (cost is linear in k)",
@@ -388,7 +398,7 @@ def run_tdlz(args):
         "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * wall_mixed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "flavor": args.flavor, "precision": "mixed",
+        "config": {"workload": workload(args.config), "flavor": args.flavor, "precision": "mixed",
                    "chains_per_gpu": len(mus), "parallelism": f"replicas{world}",
                    "ms_per_step_is": "one step of every chain of the GPU (advanced together)",
                    "l2": "inputs larger than L2 (per-step working set > 5 GB)"},
