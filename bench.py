@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--profile-apply", type=int, default=0,
                     help="run N Liouvillian applications on a shape-only bundle (for profilers)")
     ap.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also time the batched form: this many q-points (|q| = m/16 2pi/a) x "
+                         "3 NH chains in one chain set (not part of the default run)")
     ap.add_argument("--kpoints", type=int, default=0,
                     help="profiling runs only: keep the first N k points (smaller device footprint)")
     return ap.parse_args()
@@ -312,6 +315,50 @@ def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, stream, pro
         ch.close()
 
 
+def run_batched(args, local, stream):
+    """The batched form: q-points m = 1..NQ along x (|q| = m/16 2pi/a) of the same crystal,
+    three NH chains (mu = x, y, z) on each, all in one chain set -- one group per q-slot,
+    each with its own k+q plane-wave counts, advanced together and replayed from one
+    captured graph, mixed precision.  The occupied states are random orthonormal spinors
+    on the crystal's spheres (the cost of a Liouvillian pass does not depend on them)."""
+    import torch
+    from paper_2203_01120_gb300 import TDLZ_MIXED, Context
+    from synth import make_ground_state
+    ctx = Context(local, stream=stream.cuda_stream)
+    try:
+        qs, npw = [], []
+        for m in range(1, args.batched + 1):
+            gs = make_ground_state(args.config, q_2pi_a=(m / 16.0, 0.0, 0.0), solver="random")
+            npw.append([int(gs.npw_kq.min()), int(gs.npw_kq.max())])
+            qs.append(ctx.load_ground_state(gs))
+            del gs
+        slots = [q for q in qs for _ in range(3)]
+        mus = [mu for _ in qs for mu in range(3)]
+        ch = ctx.chain_create(slots, mus, args.warmup + args.steps + 1, "nh", TDLZ_MIXED)
+        try:
+            ch.advance(args.warmup)
+            ctx.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            ch.advance(args.steps)
+            ev1.record(stream)
+            ctx.synchronize()
+            wall = ev0.elapsed_time(ev1) / 1000.0
+            res = ch.read()
+        finally:
+            ch.close()
+        log(f"[bench] batched: {len(mus)} chains on {len(qs)} q-slots, "
+            f"{1000 * wall / args.steps:.2f} ms per step")
+        return {"q_points": len(qs), "chains": len(mus), "value": len(mus) * args.steps / wall,
+                "unit": "steps/s", "steps": args.steps, "ms_per_step": 1000 * wall / args.steps,
+                "npw_kq_range_per_q": npw, "status": [int(v) for v in res["status"]],
+                "what": "chain-steps/s of all chains of the set; occupied states random "
+                        "orthonormal on the crystal's spheres"}
+    finally:
+        ctx.close()
+
+
 def run_tdlz(args):
     import numpy as np
     import torch
@@ -369,6 +416,7 @@ def run_tdlz(args):
                       for i, mu in enumerate(mus))
     autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     ctx.close()
+    batched = run_batched(args, local, stream) if args.batched else None
     if rank != 0:
         return
     hbm, peak_src = measured_peaks()
@@ -426,6 +474,8 @@ def run_tdlz(args):
         "cpu_baseline": cpu,
         "status": [int(v) for v in res_e2e["status"]],
     }
+    if batched:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
 
 
