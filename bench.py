@@ -379,10 +379,15 @@ def run_tdlz(args):
     # ------------------------------------------------------------ e2e (host in/out)
     t0 = time.perf_counter()
     q = ctx.load_ground_state(gs)
+    t1 = time.perf_counter()
     ch = ctx.chain_create([q] * len(mus), mus, args.steps, args.flavor, TDLZ_MIXED)
+    ctx.synchronize()
+    t2 = time.perf_counter()
     ch.advance(args.steps)
     res_e2e = ch.read()
     e2e_wall = time.perf_counter() - t0
+    e2e_parts = {"load_s": t1 - t0, "chain_start_s": t2 - t1,
+                 "steps_and_read_s": e2e_wall - (t2 - t0)}
     ch.close()
     bundle_bytes = sum(int(np.asarray(getattr(gs, k)).nbytes) for k in (
         "kpts", "wk", "npw_k", "npw_kq", "miller_k", "miller_kq", "evals", "coeff_k", "coeff_kq",
@@ -470,7 +475,7 @@ def run_tdlz(args):
                 "h2d_bytes_per_step": bundle_bytes / args.steps,
                 "d2h_bytes_per_step": coef_bytes / args.steps,
                 "what": "load_ground_state(host bundle) + chain of K mixed steps + coefficients "
-                        "to host, through the C ABI"},
+                        "to host, through the C ABI", **e2e_parts},
         "cpu_baseline": cpu,
         "status": [int(v) for v in res_e2e["status"]],
     }

@@ -18,7 +18,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "engine.cuh"
 #include "pipeline.cuh"
@@ -655,6 +657,23 @@ __global__ void gather_component_kernel(const cx<T> *__restrict__ a, cx<T> *__re
 }  // namespace
 
 // ===================================================================== load
+// f(i) for i in [0, n) on up to 16 host threads (interleaved indices); f must not throw.
+template <class F>
+void host_parallel_for(long long n, F &&f) {
+  const long long nt =
+      std::min<long long>(n, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+  if (nt <= 1) {
+    for (long long i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (long long t = 0; t < nt; ++t)
+    th.emplace_back([&f, t, nt, n] {
+      for (long long i = t; i < n; i += nt) f(i);
+    });
+  for (auto &x : th) x.join();
+}
+
 void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   // ---- validation (host; nothing launched on failure)
   TDLZ_REQUIRE(gs != nullptr, TDLZ_ERR_ARG, "ground state is NULL");
@@ -685,8 +704,19 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     TDLZ_REQUIRE(std::isfinite(gs->wk[k]) && gs->wk[k] > 0, TDLZ_ERR_ARG, "k weights must be > 0");
   }
   auto finite_all = [](const double *p, long long n) {
-    for (long long i = 0; i < n; ++i)
-      if (!std::isfinite(p[i])) return false;
+    // chunks of 1 M values checked on the host threads
+    const long long chunk = 1 << 20, nc = (n + chunk - 1) / chunk;
+    std::vector<char> ok((size_t)nc, 1);
+    host_parallel_for(nc, [&](long long c) {
+      const long long e = std::min(n, (c + 1) * chunk);
+      for (long long i = c * chunk; i < e; ++i)
+        if (!std::isfinite(p[i])) {
+          ok[(size_t)c] = 0;
+          return;
+        }
+    });
+    for (char v : ok)
+      if (!v) return false;
     return true;
   };
   long long brd = 2LL * nk * nb * 2 * npwx * 2;
@@ -759,17 +789,17 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   // [outer][nk][rows][npwx] complex arrays in the internal order (zero padding)
   auto to_internal = [&](const double *src, long long outer, long long rws) {
     std::vector<double> dst((size_t)(outer * nk * rws * npwx * 2), 0.0);
-    for (long long o = 0; o < outer; ++o)
-      for (int k = 0; k < nk; ++k) {
-        const int *pk = perm.data() + (size_t)k * npwx;
-        for (long long r = 0; r < rws; ++r) {
-          const size_t base = (size_t)(((o * nk + k) * rws + r) * npwx) * 2;
-          for (int i = 0; i < gs->npw_kq[k]; ++i) {
-            dst[base + 2 * i] = src[base + 2 * (size_t)pk[i]];
-            dst[base + 2 * i + 1] = src[base + 2 * (size_t)pk[i] + 1];
-          }
+    host_parallel_for(outer * nk, [&](long long ok) {
+      const int k = (int)(ok % nk);
+      const int *pk = perm.data() + (size_t)k * npwx;
+      for (long long r = 0; r < rws; ++r) {
+        const size_t base = (size_t)((ok * rws + r) * npwx) * 2;
+        for (int i = 0; i < gs->npw_kq[k]; ++i) {
+          dst[base + 2 * i] = src[base + 2 * (size_t)pk[i]];
+          dst[base + 2 * i + 1] = src[base + 2 * (size_t)pk[i] + 1];
         }
       }
+    });
     return dst;
   };
   {
