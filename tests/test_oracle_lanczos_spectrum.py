@@ -110,6 +110,23 @@ def test_p7_biorthogonality(c0_chains):
         assert np.max(np.abs(ph.alpha.imag)) == 0.0
 
 
+def test_first_step_from_an_eigenvector():
+    """Started from an exact eigenvector a of the brute-force L (L a = lambda a), the NH
+    recursion (Sec. 2.5) finds alpha_1 = lambda and a right residual r at rounding level;
+    p_1 = q_1 is not a left eigenvector, so t = O(|lambda|) and beta_2 = sqrt|t^H r| is of
+    order sqrt(eps) |lambda|.  A generic start vector has beta_2 of the order of the
+    spectrum's width."""
+    lv, ph = liouvillian("C0"), particle_hole("C0")
+    ev, vec = np.linalg.eig(ph.L)
+    i = int(np.argmax(np.abs(ev)))
+    u = [lv.left_vector(l) for l in range(3)]
+    co = lanczos_nh(lv.apply, lv.apply_adjoint, ph.to_br(vec[:, i]), u, 2)
+    assert abs(co.alpha[0] - ev[i]) <= 1e-10 * abs(ev[i])
+    assert co.beta[0] <= 1e-6 * abs(ev[i])
+    gen = lanczos_nh(lv.apply, lv.apply_adjoint, lv.start_vector(0), u, 2)
+    assert gen.beta[0] >= 1e-3 * abs(ev[i])
+
+
 def test_p12_dense_vs_matrix_free():
     """NH and PHM agree step by step to rounding over 50 steps.  The J-metric PH
     is compared on the longitudinal chain (mu = z): for the transverse chains the
