@@ -315,6 +315,37 @@ def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, stream, pro
         ch.close()
 
 
+def cufft_baseline(rows, fft, device, reps=3):
+    """cuFFT (through torch.fft) on the batch of one Liouvillian pass: `rows` full-box 3D
+    transforms of the FFT grid in FP32 complex, inverse and forward, out of place, timed
+    with CUDA events after one warm-up.  The library's passes transform only the sticks and
+    planes of the spheres and include the sphere scatter and gather; cuFFT transforms the
+    whole box.  Returns milliseconds per batch, or the error."""
+    import torch
+    try:
+        dims = (1, 2, 3)
+        x = torch.randn(rows, *fft, dtype=torch.complex64, device=device)
+        out = {}
+        for name, f in (("inverse_ms", torch.fft.ifftn), ("forward_ms", torch.fft.fftn)):
+            y = f(x, dim=dims)
+            torch.cuda.synchronize(device)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(reps):
+                y = f(x, dim=dims)
+            ev1.record()
+            torch.cuda.synchronize(device)
+            out[name] = ev0.elapsed_time(ev1) / reps
+            del y
+        del x
+        torch.cuda.empty_cache()
+        return {"rows": rows, "grid": list(fft), **out,
+                "what": "torch.fft (cuFFT) full-box batched 3D FFT, complex64, out of place"}
+    except Exception as e:  # reported, never fatal to the bench line
+        return {"rows": rows, "grid": list(fft), "error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_batched(args, local, stream):
     """The batched form: q-points m = 1..NQ along x (|q| = m/16 2pi/a) of the same crystal,
     three NH chains (mu = x, y, z) on each, all in one chain set -- one group per q-slot,
@@ -421,6 +452,14 @@ def run_tdlz(args):
                       for i, mu in enumerate(mus))
     autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     ctx.close()
+    # cuFFT on the same batch as one pass (full box), beside the library's pruned passes
+    cufft = None
+    if not args.kpoints and not args.mixed_only:
+        rows = len(mus) * (2 if args.flavor == "nh" else 1) * 4 * gs.nk * gs.nocc
+        cufft = cufft_baseline(rows, tuple(int(n) for n in gs.fft), local)
+        st_ms = {k: v["ms"] / args.steps for k, v in prof.items()}
+        cufft["tdlz_inverse_ms"] = st_ms.get("scatter", 0.0) + st_ms.get("fft_inv", 0.0)
+        cufft["tdlz_forward_ms"] = st_ms.get("fft_fwd", 0.0) + st_ms.get("gather", 0.0)
     batched = run_batched(args, local, stream) if args.batched else None
     if rank != 0:
         return
@@ -479,6 +518,8 @@ def run_tdlz(args):
         "cpu_baseline": cpu,
         "status": [int(v) for v in res_e2e["status"]],
     }
+    if cufft:
+        line["cufft_baseline"] = cufft
     if batched:
         line["batched"] = batched
     print(json.dumps(line), flush=True)
