@@ -62,6 +62,17 @@ class TdlzSpectrumParams(C.Structure):
                 ("itermax", C.c_int), ("extrapolation", C.c_int)]
 
 
+def parse_autotune_report(text):
+    """{"stage/shape": (choice, ms)} from tdlz_autotune_report's "stage/shape=choice (ms)"
+    lines (the shape itself holds "=" signs; the choice follows the last one)."""
+    out = {}
+    for line in text.splitlines():
+        key, _, rest = line.rpartition("=")
+        val, _, ms = rest.partition(" (")
+        out[key] = (int(val), float(ms.rstrip(" ms)")))
+    return out
+
+
 EXTRAPOLATION = {"no": 0, "constant": 1, "osc": 2}
 
 
@@ -231,12 +242,7 @@ class Context:
         self._check(self.lib.tdlz_autotune_report(self.h, None, 0, C.byref(need)))
         buf = C.create_string_buffer(need.value + 1)
         self._check(self.lib.tdlz_autotune_report(self.h, buf, need.value + 1, C.byref(need)))
-        out = {}
-        for line in buf.value.decode().splitlines():
-            key, _, rest = line.rpartition("=")
-            val, _, ms = rest.partition(" (")
-            out[key] = (int(val), float(ms.rstrip(" ms)")))
-        return out
+        return parse_autotune_report(buf.value.decode())
 
     def vec_layout(self, qslot):
         n = C.c_int64()

@@ -56,3 +56,13 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_autotune_report_parsing():
+    from paper_2203_01120_gb300.binding import parse_autotune_report
+    text = ("density/f32/nr=124416/rows=2560/nvec=6=3 (1.7012 ms)\n"
+            "inv_x/f32/n=36/lines=3456/rows=15360=256 (1.5590 ms)\n")
+    got = parse_autotune_report(text)
+    assert got == {"density/f32/nr=124416/rows=2560/nvec=6": (3, 1.7012),
+                   "inv_x/f32/n=36/lines=3456/rows=15360": (256, 1.559)}
+    assert parse_autotune_report("") == {}
