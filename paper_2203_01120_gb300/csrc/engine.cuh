@@ -71,15 +71,15 @@ template <class T> struct SlotData {
   DevBuf vhfac;  // [Nr]   4 pi / |q+G|^2 / Nr on the Hartree sphere (real)
   DevBuf wk;     // [nk]   (real)
   DevBuf uvec;   // [3][BR] u^lambda = J sigma^lambda U (unprojected)
-  DevBuf us;     // FP32 slab path: [2][nk][nb][2][n3][n1*n2 (even)] U(r) in z-major slabs
+  DevBuf us;     // plane stages: [2][nk][nb][2][n3][n1*n2 (even)] U(r) in z-major slabs
   bool ready = false;
 };
 
 template <class T> struct Workspace {
-  DevBuf xr;    // [2][nk][nb][2][Nr] real-space response orbitals
+  DevBuf xr;    // staged pipeline: [nvec][2][nk][nb][2][Nr] real-space response orbitals
   DevBuf rho;   // [nvec][4][Nr]
   DevBuf rhopart;  // [groups][nvec][4][Nr] partial densities
-  DevBuf vpot;  // [4][Nr]
+  DevBuf vpot;  // [nvec][4][Nr]; plane stages: potential planes [nvec][n3][6][n1*n2 (even)]
   DevBuf hgrid; // [Nr] Hartree scratch
   DevBuf h;     // [BR] sphere intermediate
   DevBuf xin;   // [BR] sign-flipped input for the adjoint
@@ -87,9 +87,8 @@ template <class T> struct Workspace {
   DevBuf dmix;  // [2nk][2nb][nproj]
   DevBuf ovl;   // [2nk][nb][nb]      <U_kq|h>
   DevBuf part;  // split-K partial sums
-  DevBuf i1;    // [rows][nstick_max][n3] stick scratch
-  DevBuf i2;    // [rows][nplane_max][n2][n3] plane scratch
-  DevBuf coef;  // slab path: [nvec][2][6][Nr] complex product-coefficient planes
+  DevBuf i1;    // stick scratch: [rows][nstick_max][n3]; plane stages [rows][n3][nstick_max]
+  DevBuf i2;    // staged pipeline: [rows][nplane_max][n2][n3] plane scratch
   int nvec_cap = 0;  // stacked vectors the buffers above are sized for
   bool ready = false;
 };
@@ -114,6 +113,7 @@ struct QSlot {
   DevBuf coeff_k;        // [2][nk][nb][2][npwx] occupied k spinors (FP64; start vectors)
   // stick / plane tables of the k+q spheres (pipeline.cu)
   int nstick_max = 0, nplane_max = 0;
+  std::vector<int> nst_h, npl_h;  // sticks and planes per k (host copies)
   DevBuf st_n;    // [nk] sticks per k
   DevBuf st_map;  // [nk][nstick_max][n3] sphere index of (stick, j3) or -1
   DevBuf st_run;  // [nk][nstick_max + 1] int4 (first plane wave, run A length, run A j3, run B j3)
@@ -124,7 +124,9 @@ struct QSlot {
   DevBuf st_id;   // [nk][nplane_max][n2] stick index of (plane, j2) or -1
   int dnl_w = 0;   // nonzeros per row of D in the ELL form (padded)
   DevBuf dnl_col;  // [2nproj][dnl_w] column of each entry of dnl_val, -1 past the row's end
-  bool slab = false;  // FP32 Liouvillian runs the plane-slab real-space stages (slab.cu)
+  // the Liouvillian of each precision runs the fused plane stages (planes.cu); otherwise
+  // the staged pipeline with real-space grids in HBM (pipeline.cu)
+  bool planes32 = false, planes64 = false;
   bool tensor_gemm = true;  // FP32 V_NL / P_c reductions and updates on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;

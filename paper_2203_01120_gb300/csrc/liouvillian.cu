@@ -24,7 +24,7 @@
 
 #include "engine.cuh"
 #include "pipeline.cuh"
-#include "slab.cuh"
+#include "planes.cuh"
 #include "tc_gemm.cuh"
 
 namespace tdlz {
@@ -606,11 +606,24 @@ void alloc_workspace(QSlot &s, int nvec) {
   if (w.ready && w.nvec_cap >= nvec) return;
   const size_t c = sizeof(cx<T>), nv = (size_t)nvec;
   w.ready = false;
-  const bool slab = sizeof(T) == 4 && s.slab;  // plane-slab path: no plane buffer
-  w.xr.alloc(nv * s.rows() * s.nr * c);
+  const bool planes = sizeof(T) == 4 ? s.planes32 : s.planes64;
+  // fused plane stages: no real-space grids or plane buffer in HBM, only the stick
+  // buffer, per-chunk partial densities and the potential planes
+  if (planes) {
+    w.xr.reset();
+    w.i2.reset();
+    size_t pmax = 0;
+    for (int m = 1; m <= nvec; ++m)
+      pmax = std::max(pmax, (size_t)planes_density_chunks(s, m, c) * m);
+    w.rhopart.alloc(pmax * 4 * (size_t)s.nr * c);
+    w.vpot.alloc(nv * s.fft[2] * 6 * (size_t)planes_nnp(s) * c);
+  } else {
+    w.xr.alloc(nv * s.rows() * s.nr * c);
+    w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+    w.rhopart.alloc((size_t)kDensityGroups * nv * 4 * (size_t)s.nr * c);
+    w.vpot.alloc(nv * 4 * (size_t)s.nr * c);
+  }
   w.rho.alloc(nv * 4 * (size_t)s.nr * c);
-  w.rhopart.alloc((size_t)kDensityGroups * nv * 4 * (size_t)s.nr * c);
-  w.vpot.alloc(nv * 4 * (size_t)s.nr * c);
   w.hgrid.alloc(nv * (size_t)s.nr * c);
   w.h.alloc(nv * (size_t)s.br_elems() * c);
   w.xin.alloc(nv * (size_t)s.br_elems() * c);
@@ -622,14 +635,6 @@ void alloc_workspace(QSlot &s, int nvec) {
   size_t p2 = (size_t)32 * batch * s.nb * s.nb;
   w.part.alloc(std::max(p1, p2) * c);
   w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
-  if (slab)
-    w.i2.reset();
-  else
-    w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
-  if (slab)
-    w.coef.alloc(nv * 2 * 6 * (size_t)s.nr * sizeof(float2));
-  else
-    w.coef.reset();
   w.nvec_cap = nvec;
   w.ready = true;
 }
@@ -881,10 +886,27 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   };
   s.plan.init(gs->fft);
   build_stick_tables(s, idx_kq);
-  // TDLZ_SLAB=1 selects the plane-slab real-space stages (fused Y+X passes) where the
-  // grid allows them; the staged pipeline is the default
-  const char *slab_env = std::getenv("TDLZ_SLAB");
-  s.slab = slab_supported(s) && slab_env && slab_env[0] == '1';
+  // Real-space stages: the staged pipeline (real-space grids of every stacked vector in
+  // HBM) where its workspace, planned for six stacked vectors in both precisions, takes
+  // at most 60% of the device; otherwise the fused plane stages, whose workspace is the
+  // stick buffer.  On the 36x36x96 workload the staged pipeline is the faster of the two
+  // (its grid traffic costs less HBM time than the plane stages' extra line transforms
+  // cost issue slots).  TDLZ_PLANES=1 forces the plane stages where the grid allows
+  // them, TDLZ_PLANES=0 the staged pipeline.
+  {
+    const char *pl_env = std::getenv("TDLZ_PLANES");
+    const double rows = (double)s.rows(), per_row = (double)nr +
+                                                    (double)s.nplane_max * s.fft[1] * s.fft[2] +
+                                                    (double)s.nstick_max * s.fft[2];
+    const double staged_bytes = rows * nr * (16.0 + 8.0) + 6.0 * rows * per_row * (16.0 + 8.0);
+    size_t free_b = 0, total_b = 0;
+    TDLZ_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    bool want = staged_bytes > 0.6 * (double)total_b;
+    if (pl_env && pl_env[0] == '0') want = false;
+    if (pl_env && pl_env[0] == '1') want = true;
+    s.planes32 = want && planes_supported<float>(s);
+    s.planes64 = want && planes_supported<double>(s);
+  }
   // TDLZ_TC=0 keeps the V_NL / P_c reductions and updates on the CUDA-core GEMMs (A/B timing)
   const char *tc_env = std::getenv("TDLZ_TC");
   s.tensor_gemm = !(tc_env && tc_env[0] == '0');
@@ -950,6 +972,12 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
       1.0 / std::sqrt(s.omega), s.rows());
   TDLZ_LAUNCH_CHECK();
   fft3d<double>(s.plan, d.ur.as<double2>(), s.rows(), +1, st);
+  // plane stages read U(r) as z-major slabs; the grid-order copy is kept only while a
+  // staged pipeline (or the FP32 slabs, built lazily) still needs it
+  if (s.planes64) {
+    planes_build_u<double>(ctx, s, d.ur.as<double2>(), d.us);
+    if (s.planes32) d.ur.reset();
+  }
   // u^lambda = J sigma^lambda U on the k+q sphere (unprojected)
   d.uvec.alloc(3 * brb);
   for (int l = 0; l < 3; ++l) {
@@ -969,10 +997,14 @@ void ensure_precision(Context &ctx, QSlot &s) {
     if (!f.ready) {
       SlotData<double> &d = s.d64;
       convert_buf<float>(ctx, d.ukq, f.ukq);
-      if (s.slab)
-        slab_build_u(ctx, s, d.ur.as<double2>(), f.us);
-      else
+      if (s.planes32) {
+        if (d.us.p)
+          convert_buf<float>(ctx, d.us, f.us);  // same slab layout
+        else
+          planes_build_u<float>(ctx, s, d.ur.as<double2>(), f.us);
+      } else {
         convert_buf<float>(ctx, d.ur, f.ur);
+      }
       if (s.nproj > 0) {
         convert_buf<float>(ctx, d.beta, f.beta);
         convert_buf<float>(ctx, d.dnl, f.dnl);
@@ -1022,88 +1054,99 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
     }
     x = xin;
   }
-  cx<T> *xr = w.xr.template as<cx<T>>();
-  cx<T> *i1 = w.i1.template as<cx<T>>(), *i2 = w.i2.template as<cx<T>>();
-  const bool slab = sizeof(T) == 4 && s.slab;
-  // pruned traffic of the plane-slab stages: stick buffer (rows x nstick x n3)
-  const double S1 = (double)rows * s.nstick_max * s.fft[2];
-  // FLOPs of the x-y line transforms of one pass on the slab path (planes + columns)
-  const double xy_flops = (double)rows * s.fft[2] *
-                          (s.nplane_max + s.fft[1]) * 5.0 * s.fft[0] * std::log2((double)s.fft[0]);
-  const double z_flops = (double)rows * s.nstick_max * 5.0 * s.fft[2] * std::log2((double)s.fft[2]);
-  // 1. sphere -> real space (pruned Z, Y passes; full X pass)
-  if (slab) {
-    // sphere in, sticks out and back in, slabs out
-    ProfScope ps(pf, st, ST_FFT_INV, V * c + 2 * S1 * c + G * c, z_flops + xy_flops);
-    if constexpr (sizeof(T) == 4) {
-      sticks_inverse<T>(ctx, s, x, i1, nvec);
-      slab_inverse_yx(ctx, s, i1, xr, nvec);
-    }
-  } else {
-    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);  // profiled per stage inside
-  }
-  // 2-4. densities and HXC potentials (one set per vector)
+  cx<T> *i1 = w.i1.template as<cx<T>>();
   cx<T> *rho = w.rho.template as<cx<T>>();
   cx<T> *vp = w.vpot.template as<cx<T>>();
   cx<T> *hg = w.hgrid.template as<cx<T>>();
-  const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
-  if (use_h || use_xc) {
-    if (slab) {
-      // slabs and U (once per pass of up to 3 vectors) in, partials out and back, rho out
-      const double ng = slab_density_groups(s);
-      ProfScope ps(pf, st, ST_DENSITY,
-                   G * c + Gu * c * ((nvec + 2) / 3) + (2 * ng + 1) * 4 * nvec * nr * c,
-                   (double)nbs * nr * 40.0);
-      if constexpr (sizeof(T) == 4)
-        slab_density(ctx, s, xr, d.us.template as<float2>(), d.wk.template as<float>(),
-                     w.rhopart.template as<float2>(), rho, nvec);
-    } else {
-      ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
-                   (double)nbs * nr * 40.0);
-      launch_density<T>(ctx, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
-                        w.rhopart.template as<cx<T>>(), nk, nb, nr, nvec);
-    }
-    if (use_h) {
-      ProfScope ps(pf, st, ST_HARTREE, 8.0 * nvec * nr * c,
-                   2 * 5.0 * nvec * nr * std::log2((double)nr));
-      long long tot = (long long)nvec * nr;
-      gather_component_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(rho, hg, nr, 4 * nr, tot);
-      TDLZ_LAUNCH_CHECK();
-      fft3d<T>(s.plan, hg, nvec, -1, st);
-      scale_periodic_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
-          hg, d.vhfac.template as<T>(), nr, tot);
-      TDLZ_LAUNCH_CHECK();
-      fft3d<T>(s.plan, hg, nvec, +1, st);
-    }
-    ProfScope ps(pf, st, ST_POTENTIAL, nvec * (9 * nr * c + 10 * nr * re),
-                 16.0 * 4 * nr * nvec);
-    for (int v = 0; v < nvec; ++v) {
-      potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(
-          rho + (long long)v * 4 * nr, hg + (long long)v * nr, d.fxc.template as<T>(),
-          vp + (long long)v * 4 * nr, nr, use_h ? 1 : 0, use_xc ? 1 : 0);
-      TDLZ_LAUNCH_CHECK();
-    }
-  } else {
-    TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
-  }
-  // 5-6. local products fused into the forward X pass; pruned Y, Z passes with the
-  //      sphere gather and + (kin - e) x fused into the last one
   cx<T> *h = w.h.template as<cx<T>>();
-  if (slab) {
-    // coefficients written and read back, slabs and U in, sticks out and back in,
-    // x read and h written on the sphere
-    ProfScope ps(pf, st, ST_FFT_FWD,
-                 4 * nvec * nr * (c + re) + 2 * nvec * nr * 48.0 + G * c + Gu * c + 2 * S1 * c +
-                     2 * V * c,
-                 xy_flops + z_flops + (double)nbs * nr * 64.0);
-    if constexpr (sizeof(T) == 4) {
-      slab_product_forward(ctx, s, xr, d.us.template as<float2>(), vp,
-                           d.vloc.template as<float>(), d.bfield.template as<float>(),
-                           w.coef.template as<float2>(), i1, nvec);
+  const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
+  // Hartree at q (Eq. v_H_q): rho'_0 -> G, 4 pi / |q+G|^2 on the density sphere, -> r
+  auto hartree = [&]() {
+    ProfScope ps(pf, st, ST_HARTREE, 8.0 * nvec * nr * c,
+                 2 * 5.0 * nvec * nr * std::log2((double)nr));
+    long long tot = (long long)nvec * nr;
+    gather_component_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(rho, hg, nr, 4 * nr, tot);
+    TDLZ_LAUNCH_CHECK();
+    fft3d<T>(s.plan, hg, nvec, -1, st);
+    scale_periodic_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
+        hg, d.vhfac.template as<T>(), nr, tot);
+    TDLZ_LAUNCH_CHECK();
+    fft3d<T>(s.plan, hg, nvec, +1, st);
+  };
+  const bool planes = sizeof(T) == 4 ? s.planes32 : s.planes64;
+  if (planes) {
+    // 1-6 on the fused plane stages (planes.cu): the stick buffer is the only real-space
+    // intermediate in HBM.  Exact work of one pass: sticks and planes of every row's k.
+    const int n2 = s.fft[1], n3 = s.fft[2];
+    double st_rows = 0, yx_lines = 0;
+    for (int k = 0; k < nk; ++k) {
+      st_rows += 4.0 * nb * s.nst_h[k];
+      yx_lines += 4.0 * nb * (s.npl_h[k] + n2);
+    }
+    const double S1 = nvec * st_rows * n3;  // stick buffer elements touched
+    const double z_fl = nvec * st_rows * 5.0 * n3 * std::log2((double)n3);
+    const double yx_fl = nvec * yx_lines * n3 * 5.0 * n2 * std::log2((double)n2);
+    const double pot_bytes = 6.0 * nvec * nr * c;
+    {
+      // sphere in, sticks out
+      ProfScope ps(pf, st, ST_SCATTER, V * c + S1 * c, z_fl);
+      sticks_inverse<T>(ctx, s, x, i1, nvec);
+    }
+    if (use_h || use_xc) {
+      // sticks and U planes in, partial densities out and back, rho out
+      const double nch = planes_density_chunks(s, nvec, sizeof(cx<T>));
+      ProfScope ps(pf, st, ST_DENSITY, S1 * c + Gu * c + (2 * nch + 1) * 4 * nvec * nr * c,
+                   yx_fl + (double)nbs * nr * 40.0);
+      planes_density<T>(ctx, s, i1, d.us.template as<cx<T>>(), d.wk.template as<T>(),
+                        w.rhopart.template as<cx<T>>(), rho, nvec);
+    }
+    if (use_h) hartree();
+    {
+      ProfScope ps(pf, st, ST_POTENTIAL,
+                   nvec * (5 * nr * c + 14 * nr * re) + pot_bytes, 16.0 * 4 * nr * nvec);
+      planes_potential<T>(ctx, s, rho, hg, d.fxc.template as<T>(), d.vloc.template as<T>(),
+                          d.bfield.template as<T>(), vp, nvec, use_h, use_xc);
+    }
+    {
+      // sticks in and out (in place), U planes, potential planes once per CTA
+      ProfScope ps(pf, st, ST_PRODUCT, 2 * S1 * c + Gu * c + pot_bytes,
+                   2 * yx_fl + (double)nbs * nr * 64.0);
+      planes_product_forward<T>(ctx, s, i1, d.us.template as<cx<T>>(), vp, nvec,
+                                [&] { sticks_inverse<T>(ctx, s, x, i1, nvec); });
+    }
+    {
+      // sticks in; x read, h written on the sphere and zero on the padding
+      ProfScope ps(pf, st, ST_GATHER, S1 * c + 3 * V * c, z_fl);
       sticks_forward<T>(ctx, s, x, i1, d.kin.template as<T>(), d.evals.template as<T>(), h,
                         nvec);
     }
   } else {
+    cx<T> *xr = w.xr.template as<cx<T>>();
+    cx<T> *i2 = w.i2.template as<cx<T>>();
+    // 1. sphere -> real space (pruned Z, Y passes; full X pass)
+    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);  // profiled per stage inside
+    // 2-4. densities and HXC potentials (one set per vector)
+    if (use_h || use_xc) {
+      {
+        ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
+                     (double)nbs * nr * 40.0);
+        launch_density<T>(ctx, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
+                          w.rhopart.template as<cx<T>>(), nk, nb, nr, nvec);
+      }
+      if (use_h) hartree();
+      ProfScope ps(pf, st, ST_POTENTIAL, nvec * (9 * nr * c + 10 * nr * re),
+                   16.0 * 4 * nr * nvec);
+      for (int v = 0; v < nvec; ++v) {
+        potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(
+            rho + (long long)v * 4 * nr, hg + (long long)v * nr, d.fxc.template as<T>(),
+            vp + (long long)v * 4 * nr, nr, use_h ? 1 : 0, use_xc ? 1 : 0);
+        TDLZ_LAUNCH_CHECK();
+      }
+    } else {
+      TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
+    }
+    // 5-6. local products; pruned X, Y, Z forward passes with the sphere gather and
+    //      + (kin - e) x fused into the last one
     pipeline_forward<T>(ctx, s, x, xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(),
                         d.bfield.template as<T>(), vp, d.kin.template as<T>(),
                         d.evals.template as<T>(), i1, i2, h, nvec);  // profiled inside

@@ -876,6 +876,9 @@ void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
     nsm = std::max(nsm, cnt);
     npm = std::max(npm, (int)planes[k].size());
   }
+  // even, so that each (row, plane) run of the [row][j3][stick] buffer starts on a 16-byte
+  // boundary in FP32 (the plane stages stage it with 16-byte asynchronous copies)
+  nsm = (nsm + 1) & ~1;
   s.nstick_max = nsm;
   s.nplane_max = npm;
   std::vector<int> nst(nk), smap((size_t)nk * nsm * n3, -1), npl(nk), plj((size_t)nk * npm, -1),
@@ -948,6 +951,8 @@ void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
   up(s.pl_j1, plj);
   up(s.pl_of, plof);
   up(s.st_id, sid);
+  s.nst_h = nst;
+  s.npl_h = npl;
 }
 
 // Element counts and FLOPs of one pass over nvec stacked vectors, for the
@@ -1182,7 +1187,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
   }
 }
 
-// Z passes alone, stick buffer in [row][j3][stick] order (slab-fused stages).
+// Z passes alone, stick buffer in [row][j3][stick] order (fused plane stages).
 template <class T>
 void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec) {
   cudaStream_t st = ctx.stream;
@@ -1238,8 +1243,11 @@ void sticks_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *i1t, co
 }
 
 template void sticks_inverse<float>(Context &, QSlot &, const float2 *, float2 *, int);
+template void sticks_inverse<double>(Context &, QSlot &, const double2 *, double2 *, int);
 template void sticks_forward<float>(Context &, QSlot &, const float2 *, const float2 *,
                                     const float *, const float *, float2 *, int);
+template void sticks_forward<double>(Context &, QSlot &, const double2 *, const double2 *,
+                                     const double *, const double *, double2 *, int);
 template void pipeline_inverse<double>(Context &, QSlot &, const double2 *, double2 *, double2 *,
                                        double2 *, int);
 template void pipeline_inverse<float>(Context &, QSlot &, const float2 *, float2 *, float2 *,

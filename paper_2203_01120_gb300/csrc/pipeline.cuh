@@ -23,7 +23,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
                       cx<T> *i1, cx<T> *i2, cx<T> *h, int nvec);
 
 // Z passes alone, with the stick buffer i1t in [nvec*rows][n3][nstick_max] order
-// (slab-fused stages): sphere -> sticks, and sticks -> sphere + (kin - e) x.
+// (fused plane stages, planes.cu): sphere -> sticks, and sticks -> sphere + (kin - e) x.
 template <class T>
 void sticks_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *i1t, int nvec);
 template <class T>

@@ -114,8 +114,51 @@ __device__ __forceinline__ void rstages(cx<T> (&a)[N], const RegTw<T, N> &tw) {
   if constexpr (sizeof...(Rs) > 0) rstages<T, N, DIR, NS * R, Rs...>(a, tw);
 }
 
-// Radix plans of the lengths handled in registers.
+// Radix plans of the lengths handled in registers (3, 4, 6, 8, 9, 15, 18 are the
+// per-lane parts of lines split over two or three lanes).
 template <int N> struct RegPlan;
+template <> struct RegPlan<3> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[3], const RegTw<T, 3> &tw) {
+    rstages<T, 3, DIR, 1, 3>(a, tw);
+  }
+};
+template <> struct RegPlan<4> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[4], const RegTw<T, 4> &tw) {
+    rstages<T, 4, DIR, 1, 4>(a, tw);
+  }
+};
+template <> struct RegPlan<6> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[6], const RegTw<T, 6> &tw) {
+    rstages<T, 6, DIR, 1, 2, 3>(a, tw);
+  }
+};
+template <> struct RegPlan<8> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[8], const RegTw<T, 8> &tw) {
+    rstages<T, 8, DIR, 1, 4, 2>(a, tw);
+  }
+};
+template <> struct RegPlan<9> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[9], const RegTw<T, 9> &tw) {
+    rstages<T, 9, DIR, 1, 3, 3>(a, tw);
+  }
+};
+template <> struct RegPlan<15> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[15], const RegTw<T, 15> &tw) {
+    rstages<T, 15, DIR, 1, 3, 5>(a, tw);
+  }
+};
+template <> struct RegPlan<18> {
+  template <class T, int DIR>
+  __device__ static void run(cx<T> (&a)[18], const RegTw<T, 18> &tw) {
+    rstages<T, 18, DIR, 1, 2, 3, 3>(a, tw);
+  }
+};
 template <> struct RegPlan<12> {
   template <class T, int DIR>
   __device__ static void run(cx<T> (&a)[12], const RegTw<T, 12> &tw) {

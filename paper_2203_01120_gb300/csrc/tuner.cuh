@@ -47,6 +47,14 @@ struct Tuner {
   template <class F>
   int pick(cudaStream_t stream, const std::string &key, const std::vector<int> &cands, int dflt,
            F &&run) {
+    return pick(stream, key, cands, dflt, run, [] {});
+  }
+  // For a stage that overwrites its own input: prep() enqueues what recreates that input
+  // and runs (untimed) before every timed candidate run, so each candidate sees the
+  // same input and the last run leaves the stage's true output.
+  template <class F, class P>
+  int pick(cudaStream_t stream, const std::string &key, const std::vector<int> &cands, int dflt,
+           F &&run, P &&prep) {
     auto it = choice.find(key);
     if (it != choice.end()) {
       run(it->second);
@@ -74,7 +82,9 @@ struct Tuner {
     TDLZ_CUDA_TRY(cudaEventCreate(&e1));
     int best = dflt;
     float tbest = -1.f;
-    for (int c : cands) {  // each run also leaves the outputs, identical for every candidate
+    for (size_t ci = 0; ci < cands.size(); ++ci) {  // each run leaves the same outputs
+      const int c = cands[ci];
+      if (ci > 0) prep();
       TDLZ_CUDA_TRY(cudaEventRecord(e0, stream));
       run(c);
       TDLZ_CUDA_TRY(cudaEventRecord(e1, stream));

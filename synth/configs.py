@@ -183,13 +183,15 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
                       dense_max: int = 2400, log=None, solver: str = "auto",
                       self_consistent: bool = False, b_ext: float = 0.0,
                       scf_tol: float = 1e-11, scf_mix: float = 0.5,
-                      scf_iter: int = 400) -> GroundState:
+                      scf_iter: int = 400, kgrid=None) -> GroundState:
     """Build the seeded ground-state bundle for config ``name``.
 
     collinear=True gives the special case of a uniform field along z with no
     spin-orbit coupling ([H, S_z] = 0).  solver="random" skips the
     diagonalisation and fills the occupied states with random orthonormal
     spinors (same shapes; for kernel profiling only, not a ground state).
+    kgrid overrides the config's Monkhorst-Pack grid (e.g. a few k points of a large
+    cell for tests that need its FFT grid and spheres but not all its k points).
     self_consistent=True replaces the model field by the exchange field of the
     ground state's own magnetisation (exchange_field) plus a uniform external field
     b_ext along z, iterated with linear mixing until the field changes by less than
@@ -206,6 +208,8 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
         cfg.q_2pi_a = tuple(q_2pi_a)
     if nocc is not None:
         cfg.nocc = nocc
+    if kgrid is not None:
+        cfg.kgrid = tuple(kgrid)
     if collinear:
         cfg.b_noncollinear = 0.0
         cfg.lam_so_scale = 0.0

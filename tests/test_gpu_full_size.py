@@ -104,6 +104,19 @@ def test_full_size_sampled_k_mixed(outputs, oracle_sampled):
     assert err <= 2e-5, err
 
 
+def test_full_size_plane_stages_sampled_k(torch, ctx, outputs, oracle_sampled, monkeypatch):
+    """The same operator through the fused plane stages (forced; the staged pipeline is
+    the default at this size): sampled k points against the oracle, FP64 and mixed."""
+    monkeypatch.setenv("TDLZ_PLANES", "1")
+    q = ctx.load_ground_state(c2_state())
+    x = outputs[0]
+    ks = list(SAMPLED_K)
+    y64 = apply_gpu(torch, ctx, q, x)
+    assert rel(y64[:, ks], oracle_sampled[:, ks]) <= 1e-12
+    y32 = apply_gpu(torch, ctx, q, x, mixed=True)
+    assert rel(y32[:, ks], oracle_sampled[:, ks]) <= 2e-5
+
+
 def test_full_size_mixed_against_fp64_everywhere(outputs):
     gs = c2_state()
     _, y64, y32 = outputs

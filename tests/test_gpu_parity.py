@@ -93,12 +93,12 @@ def test_apply_mixed(torch, ctx, name):
     assert err <= 2e-5, err
 
 
-@pytest.mark.parametrize("env", [{"TDLZ_SLAB": "1"}, {"TDLZ_TC": "0"}, {"TDLZ_SLAB": "1", "TDLZ_TC": "0"}])
+@pytest.mark.parametrize("env", [{"TDLZ_TC": "0"}])
 @pytest.mark.parametrize("name", ["C0K", "C1"])
 def test_apply_mixed_alternative_paths(torch, ctx, name, env, monkeypatch):
-    """The mixed-precision Liouvillian through its alternative code paths (chosen per
-    q-slot at load): the plane-slab real-space stages and the CUDA-core reduction
-    GEMMs in place of the tensor-core ones."""
+    """The mixed-precision Liouvillian through its alternative code path (chosen per
+    q-slot at load): the CUDA-core reduction GEMMs in place of the tensor-core ones
+    (the fused plane stages have their own file, test_gpu_planes.py)."""
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     q = ctx.load_ground_state(ground_state(name))
