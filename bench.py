@@ -11,9 +11,14 @@ non-Hermitian flavour used by default, one for the pseudo-Hermitian flavours.
 Reported (one JSON line on rank 0):
   value          mixed-precision steps/s (FP32 vectors and arithmetic, FP64 scalars)
   fp64           the FP64 path's steps/s
-  chi_rel_err    ||chi_mixed - chi_fp64|| / ||chi_fp64|| at eta = 10 meV on 0-100 meV
-  roofline       dominant stage of the mixed step against the measured HBM peak
-  cpu_baseline   the FP64 CPU oracle on a one-k-point sample of the same workload
+  flavors        steps/s of the mixed path for each Lanczos flavour (NH: two Liouvillian
+                 applications per step, PH: one)
+  chi            mixed vs FP64 chi(omega) at eta = 10 meV on 0-100 meV, per column
+  roofline       the step against its algorithmic work (bytes and flops of one step from
+                 the per-application counts of the method) and the FP32 / HBM peaks, with
+                 the dominant kernel's own figures beside it
+  cpu_baseline   the FP64 CPU oracle: one full step of the same workload (C2), or a
+                 one-k-point sample scaled by the k count where a full step takes too long
   e2e            host ground state in -> coefficients out, through the C ABI
 
 --impl reference runs the oracle (CPU) as the reference arm.
@@ -58,8 +63,13 @@ def parse():
     ap.add_argument("--config", default="C2")
     # NH by default: on the synthetic C2 model D + K is indefinite (the positive-definite
     # metric does not exist) and the J-metric start vector has a J-norm ~1e-3 of its norm
-    ap.add_argument("--flavor", default="nh", choices=["ph", "phm", "nh"])
-    ap.add_argument("--chi-steps", type=int, default=60)
+    ap.add_argument("--flavor", default=None, choices=["ph", "phm", "nh"],
+                    help="default: nh on C2 (its D + K is indefinite), ph on C3")
+    ap.add_argument("--chi-steps", type=int, default=500,
+                    help="length of the mixed and FP64 chains of the chi error (C4: 500)")
+    ap.add_argument("--states", default="auto", choices=["auto", "random"],
+                    help="occupied states: auto = diagonalised on C0-C2, random orthonormal "
+                         "on larger cells (the cost of a step does not depend on them)")
     ap.add_argument("--chains", type=int, default=3, choices=[1, 2, 3],
                     help="chi columns per GPU (x, y, z), advanced together")
     ap.add_argument("--tol", type=float, default=1e-9)
@@ -75,7 +85,10 @@ def parse():
                          "3 NH chains in one chain set (not part of the default run)")
     ap.add_argument("--kpoints", type=int, default=0,
                     help="profiling runs only: keep the first N k points (smaller device footprint)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.flavor is None:
+        a.flavor = "ph" if a.config in ("C3", "C5") else "nh"
+    return a
 
 
 def log(*a):
@@ -160,13 +173,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def make_workload(cfg, tol, bundle=None):
+def random_states(cfg, states):
+    """Shape-only bundles (random orthonormal occupied states) on the large cells, where
+    the eigensolver would take tens of minutes and a step costs the same either way."""
+    return states == "random" or (states == "auto" and cfg in ("C3", "C5"))
+
+
+def make_workload(cfg, tol, bundle=None, states="auto"):
     from synth import GroundState, make_ground_state
     t = time.time()
     if bundle and os.path.exists(bundle):
         gs = GroundState.load(bundle)
         gs.meta = {"gap_min": float("nan"), "resid_max": float("nan")}
         log(f"[bench] ground state {cfg} loaded from {bundle}")
+        return gs
+    if random_states(cfg, states):
+        gs = make_ground_state(cfg, solver="random")
+        log(f"[bench] shape-only ground state {cfg}: npwx={gs.npwx} nk={gs.nk} "
+            f"nocc={gs.nocc} ({time.time() - t:.1f} s)")
         return gs
     gs = make_ground_state(cfg, tol=tol, log=log)
     if bundle:
@@ -188,11 +212,14 @@ def sample_bundle(gs, nk_sample=1):
         beta_kq=gs.beta_kq[s])
 
 
-def oracle_step_time(gs, nsteps=1, flavor="phm"):
-    """Seconds per Lanczos step of the FP64 oracle on a one-k-point sample, scaled by nk."""
+def oracle_step_time(gs, nsteps=1, flavor="phm", nk_sample=None):
+    """Seconds per Lanczos step of the FP64 oracle: the whole bundle (nk_sample None), or
+    its first nk_sample k points with the time scaled by nk / nk_sample (the cost is
+    linear in k).  Returns (seconds per full step, measured seconds, k points run)."""
     from oracle.liouvillian import Liouvillian
     from oracle.lanczos import lanczos_nh, lanczos_ph, lanczos_phm
-    sub = sample_bundle(gs, 1)
+    nks = gs.nk if nk_sample is None else min(nk_sample, gs.nk)
+    sub = gs if nks == gs.nk else sample_bundle(gs, nks)
     lv = Liouvillian(sub)
     v = lv.start_vector(0)
     u = [lv.left_vector(l) for l in range(3)]
@@ -206,7 +233,7 @@ def oracle_step_time(gs, nsteps=1, flavor="phm"):
     el = time.perf_counter() - t
     # phm spends one extra L product before its first step; count it as a step
     per = el / (nsteps + (1 if flavor == "phm" else 0))
-    return per * gs.nk, el
+    return per * gs.nk / nks, el, nks
 
 
 def cpu_info():
@@ -224,23 +251,30 @@ def cpu_info():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores, rank 0
+    only.  Each step is a bounded sample of the workload (one Lanczos step restricted to
+    k point 0); value is that time scaled to steps/s of the whole workload (cost linear
+    in k), ms_per_step the sample's measured time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import numpy as np  # noqa: F401
-    gs = make_workload(args.config, args.tol, args.bundle)
+    gs = make_workload(args.config, args.tol, args.bundle, args.states)
     cores, model = cpu_info()
-    times = []
+    sample_s, full_s = [], []
     for i in range(args.warmup + args.steps):
-        per, _ = oracle_step_time(gs, 1, args.flavor)
+        per_full, el, _ = oracle_step_time(gs, 1, args.flavor, nk_sample=1)
         if i >= args.warmup:
-            times.append(per)
-    t = sum(times)
-    value = args.steps / t
+            sample_s.append(el)
+            full_s.append(per_full)
+    value = args.steps / sum(full_s)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000 * sum(sample_s) / args.steps,
+        "ms_per_step_is": "measured time of one sampled step (k point 0 only); value scales "
+                          f"it by the {gs.nk} k points of the workload",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(args.config), "flavor": args.flavor},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
@@ -282,6 +316,45 @@ def ncu_traffic(args, stage):
     if args.kpoints or args.flavor != "nh" or args.chains != 3:
         return None
     return NCU_TRAFFIC.get((args.config, stage))
+
+
+def algorithmic_work(gs, flavor, chains, elem):
+    """Algorithmic bytes and flops of one Lanczos step of `chains` chains of one q-point,
+    from the per-application counts of the method: V = 2 sides x Nk x Nb x 2 spinor
+    components x Np complex numbers per response vector (Np the mean k+q sphere), elem
+    bytes per complex number.
+      bytes  NH: 6V per chain (q, p in; L q, L^H p out; q, p of the previous step) + the
+             occupied orbitals U_k, U_k+q (2V) shared by the chains of one q + the
+             projector table Nk Nbeta Np; PH: 3V per chain instead of 6V.
+      flops  per application: FFTs 2 Nk Nb 4 x 5 Nr log2 Nr x 0.56 (pruned to the sphere),
+             contractions 2 Nk (16 Nb^2 2 Np + 16 Nbeta Nb 2 Np), pointwise 110 per grid
+             point and band-side; NH applies L twice per chain and step, PH once."""
+    import math
+    import numpy as np
+    s_, ns = 2, 2
+    nk, nb, nproj = gs.nk, gs.nocc, gs.nproj
+    npw = float(np.mean(gs.npw_kq))
+    nr = int(np.prod(gs.fft))
+    v = s_ * nk * nb * ns * npw
+    nvec_terms, apps = (6, 2) if flavor == "nh" else (3, 1)
+    bytes_ = chains * nvec_terms * v * elem + 2 * v * elem + nk * nproj * npw * elem
+    fft = s_ * nk * nb * 4 * (5 * nr * math.log2(nr) * 0.56)
+    gemm = s_ * nk * (16 * nb * nb * ns * npw + 16 * nproj * nb * ns * npw)
+    point = 110 * s_ * nk * nb * nr
+    return bytes_, chains * apps * (fft + gemm + point)
+
+
+def fp32_peak_tflops(device=0):
+    """FP32 vector peak derived from unit counts: SMs x 128 FP32 lanes x 2 flop (FMA) x
+    the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
 
 
 def chain_steps_per_s(ctx, q, mus, flavor, precision, warmup, steps, stream, profile=False):
@@ -346,6 +419,42 @@ def cufft_baseline(rows, fft, device, reps=3):
         return {"rows": rows, "grid": list(fft), "error": f"{type(e).__name__}: {e}"[:200]}
 
 
+def cufft_pruned_baseline(rows, fft, nsm, npm, device, reps=3):
+    """cuFFT (torch.fft) driven the same pruned way as the library's passes, on the batch
+    of one pass: batched 1D transforms along the sphere's sticks (rows x nsm lines of
+    n3), along y on its planes (rows x npm x n3 lines of n2), along x over the box
+    (rows x n2 x n3 lines of n1), complex64, out of place.  The gathers and scatters
+    between the stages (done by the library's passes) are not included.  Returns
+    milliseconds per batch for each direction, or the error."""
+    import torch
+    try:
+        n1, n2, n3 = fft
+        out = {}
+        for name, f in (("inverse_ms", torch.fft.ifft), ("forward_ms", torch.fft.fft)):
+            total = 0.0
+            for shape, dim in (((rows, nsm, n3), 2), ((rows, npm, n2, n3), 2),
+                               ((rows, n1, n2 * n3), 1)):
+                x = torch.randn(*shape, dtype=torch.complex64, device=device)
+                y = f(x, dim=dim)
+                torch.cuda.synchronize(device)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                for _ in range(reps):
+                    y = f(x, dim=dim)
+                ev1.record()
+                torch.cuda.synchronize(device)
+                total += ev0.elapsed_time(ev1) / reps
+                del x, y
+                torch.cuda.empty_cache()
+            out[name] = total
+        return {"rows": rows, "grid": list(fft), "sticks": nsm, "planes": npm, **out,
+                "what": "torch.fft (cuFFT) batched 1D passes on the sticks, the planes and the "
+                        "box, complex64, out of place, without the gathers between passes"}
+    except Exception as e:  # reported, never fatal to the bench line
+        return {"rows": rows, "grid": list(fft), "error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_batched(args, local, stream):
     """The batched form: q-points m = 1..NQ along x (|q| = m/16 2pi/a) of the same crystal,
     three NH chains (mu = x, y, z) on each, all in one chain set -- one group per q-slot,
@@ -390,6 +499,24 @@ def run_batched(args, local, stream):
         ctx.close()
 
 
+def sphere_sticks_planes(gs):
+    """Largest number of (m1, m2) sticks and of m1 planes over the k+q spheres."""
+    import numpy as np
+    nsm = npm = 0
+    for k in range(gs.nk):
+        m = np.asarray(gs.miller_kq[k][:int(gs.npw_kq[k])])
+        nsm = max(nsm, len({(int(a), int(b)) for a, b in m[:, :2]}))
+        npm = max(npm, len(set(int(a) for a in m[:, 0])))
+    return nsm, npm
+
+
+def chi_column_errors(c32, c64):
+    """Per chi column mu: max over lambda of ||chi32 - chi64||_2 / ||chi64[mu][mu]||_2."""
+    import numpy as np
+    return [float(np.linalg.norm(c32[i] - c64[i], axis=1).max() / np.linalg.norm(c64[i][i]))
+            for i in range(len(c64))]
+
+
 def run_tdlz(args):
     import numpy as np
     import torch
@@ -400,9 +527,10 @@ def run_tdlz(args):
     torch.cuda.set_device(local)
     from paper_2203_01120_gb300 import TDLZ_FP64, TDLZ_MIXED, Context, build_ext
     build_ext.build()
-    gs = make_workload(args.config, args.tol, args.bundle)
+    gs = make_workload(args.config, args.tol, args.bundle, args.states)
     if args.kpoints:  # profiling captures only: the first k points of the workload
         gs = sample_bundle(gs, args.kpoints)
+    chi_steps = args.chi_steps if args.config in ("C2", "C4") else min(args.chi_steps, 20)
     # replicas: every rank runs the chi columns mus (the paper's ipol = 4: x, y, z)
     mus = list(range(args.chains))
     stream = torch.cuda.Stream(device=local)
@@ -436,27 +564,61 @@ def run_tdlz(args):
     # profiled pass (per-stage CUDA events on the library stream) for the roofline
     _, _, _, prof, _ = chain_steps_per_s(ctx, q, mus, args.flavor, TDLZ_MIXED, 1, args.steps,
                                          stream, profile=True)
+    flavors = {args.flavor: {"value": len(mus) * args.steps / wall_mixed, "unit": "steps/s",
+                             "ms_per_step": 1000 * wall_mixed / args.steps,
+                             "l_applications_per_step": len(mus) * (2 if args.flavor == "nh" else 1)}}
+    if not args.mixed_only:
+        for fl in ("nh", "ph"):
+            if fl in flavors:
+                continue
+            sps, wall, _, _, res = chain_steps_per_s(ctx, q, mus, fl, TDLZ_MIXED, args.warmup,
+                                                     args.steps, stream)
+            flavors[fl] = {"value": sps, "unit": "steps/s", "ms_per_step": 1000 * wall / args.steps,
+                           "l_applications_per_step": len(mus) * (2 if fl == "nh" else 1),
+                           "status": [int(v) for v in res["status"]]}
     fp64_steps = max(3, args.steps // 4)
-    m = args.chi_steps
+    m = chi_steps
+    chi = None
     if args.mixed_only:  # profiling runs: the mixed chains above are the whole workload
-        sps_fp64, wall_fp64, prof64, chi_err = None, None, {}, None
+        sps_fp64, wall_fp64, prof64 = None, None, {}
     else:
         sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(
             ctx, q, mus, args.flavor, TDLZ_FP64, 1, fp64_steps, stream, profile=True)
-        # ------------------------------------------------------------ chi error mixed vs FP64
+        # ------------------------------------------------ chi error mixed vs FP64
         r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)
         r32 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
-        c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1)
-        c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1)
-        chi_err = max(float(np.linalg.norm(c32[i] - c64[i]) / np.linalg.norm(c64[i][mu]))
-                      for i, mu in enumerate(mus))
+        chi = {"steps": m, "omega_mev": [0.0, 100.0, 0.1], "eta_mev": 10.0, "tolerance": 1e-4,
+               "norm": "per column mu: max over lambda ||chi_mixed - chi_fp64|| / ||chi_fp64[mu][mu]||"}
+        for mm in sorted({m, min(m, 100)}):
+            c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
+            c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
+            chi[f"rel_err_{mm}"] = chi_column_errors(c32, c64)
+        chi["status"] = [int(v) for v in r32["status"]] + [int(v) for v in r64["status"]]
+        # conditioning probe: the same mixed chains through the other real-space path
+        # (same operator and precision, different rounding order); where the two FP32
+        # results differ by as much as FP32 differs from FP64, the chi of that chain
+        # length is not determined to that precision by any FP32 computation
+        if args.config in ("C2", "C4"):
+            os.environ["TDLZ_PLANES"] = "1"
+            try:
+                q2 = ctx.load_ground_state(gs)
+            finally:
+                del os.environ["TDLZ_PLANES"]
+            r32b = ctx.lanczos_run([q2] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
+            for mm in sorted({m, min(m, 100)}):
+                ca = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
+                cb = ctx.spectrum(r32b, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
+                chi[f"fp32_rounding_spread_{mm}"] = chi_column_errors(cb, ca)
     autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     ctx.close()
-    # cuFFT on the same batch as one pass (full box), beside the library's pruned passes
+    # cuFFT on the same batch as one pass: full box, and driven the same pruned way
     cufft = None
     if not args.kpoints and not args.mixed_only:
         rows = len(mus) * (2 if args.flavor == "nh" else 1) * 4 * gs.nk * gs.nocc
-        cufft = cufft_baseline(rows, tuple(int(n) for n in gs.fft), local)
+        fft = tuple(int(n) for n in gs.fft)
+        cufft = {"full_box": cufft_baseline(rows, fft, local)}
+        nsm, npm = sphere_sticks_planes(gs)
+        cufft["pruned"] = cufft_pruned_baseline(rows, fft, nsm, npm, local)
         st_ms = {k: v["ms"] / args.steps for k, v in prof.items()}
         cufft["tdlz_inverse_ms"] = st_ms.get("scatter", 0.0) + st_ms.get("fft_inv", 0.0)
         cufft["tdlz_forward_ms"] = st_ms.get("fft_fwd", 0.0) + st_ms.get("gather", 0.0)
@@ -464,23 +626,29 @@ def run_tdlz(args):
     if rank != 0:
         return
     hbm, peak_src = measured_peaks()
-    # dominant stage of the mixed step
+    # dominant stage of the mixed step, against its own design traffic
     stages = {k: v for k, v in prof.items() if v["launches"] > 0 and v["ms"] > 0}
     top = max(stages, key=lambda k: stages[k]["ms"])
     st = stages[top]
     nl = st["launches"]
     per_launch_s = st["ms"] / 1000.0 / nl
     bytes_launch = st["bytes"] / nl
-    achieved = bytes_launch / per_launch_s / 1e9
-    step_bytes = sum(v["bytes"] for v in stages.values()) / args.steps
-    step_ms = sum(v["ms"] for v in stages.values()) / args.steps
+    design_bytes_step = sum(v["bytes"] for v in stages.values()) / args.steps
+    # the step against the algorithmic work of the method
+    alg_bytes, alg_flops = algorithmic_work(gs, args.flavor, len(mus), 8)
+    step_s = wall_mixed / args.steps
+    peak32, src32 = fp32_peak_tflops(local)
+    achieved_tf = alg_flops / step_s / 1e12
     cores, model = cpu_info()
     cpu = None
     if not args.no_cpu_baseline:
-        per, el = oracle_step_time(gs, 1, args.flavor)
+        full = args.config in ("C1", "C2")  # one full step is ~40 s of oracle on C2
+        per, el, nks = oracle_step_time(gs, 1, args.flavor, nk_sample=None if full else 1)
         cpu = {"value": 1.0 / per, "unit": "steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"one FP64 oracle Lanczos step ({args.flavor}) restricted to k point 0 of "
-                         f"{gs.nk}, {el:.1f} s, scaled x{gs.nk} (cost linear in k)",
+               "sample": (f"one full FP64 oracle Lanczos step ({args.flavor}, one chain, all "
+                          f"{gs.nk} k points), {el:.1f} s" if nks == gs.nk else
+                          f"one FP64 oracle Lanczos step ({args.flavor}) restricted to k point 0 "
+                          f"of {gs.nk}, {el:.1f} s, scaled x{gs.nk} (cost linear in k)"),
                "cpu": model}
     line = {
         "metric": METRIC,
@@ -492,20 +660,34 @@ def run_tdlz(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": workload(args.config), "flavor": args.flavor, "precision": "mixed",
                    "chains_per_gpu": len(mus), "parallelism": f"replicas{world}",
+                   "occupied_states": "random orthonormal (shape only)"
+                   if random_states(args.config, args.states) else "diagonalised",
                    "ms_per_step_is": "one step of every chain of the GPU (advanced together)",
                    "l2": "inputs larger than L2 (per-step working set > 5 GB)"},
+        "flavors": flavors,
         "fp64": None if sps_fp64 is None else {
             "value": sps_fp64, "unit": "steps/s", "steps": fp64_steps,
             "ms_per_step": 1000 * wall_fp64 / fp64_steps,
             "roofline": fp64_roofline(prof64)},
-        "chi_rel_err": chi_err, "chi_steps": m, "chi_tolerance": 1e-4,
-        "roofline": {"bound": "hbm", "stage": top, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": ncu_traffic(args, top), "traffic_unit": "bytes per launch",
-                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src},
-        "step_roofline": {"alg_bytes_per_step": step_bytes, "ms_per_step_profiled": step_ms,
-                          "achieved_gbs": step_bytes / (step_ms / 1000) / 1e9,
-                          "frac_hbm": step_bytes / (step_ms / 1000) / 1e9 / hbm},
+        "chi": chi,
+        "roofline": {
+            "bound": "alu", "achieved": achieved_tf, "peak": peak32, "unit": "TFLOP/s",
+            "frac": achieved_tf / peak32, "peak_source": src32,
+            "scope": "the whole mixed step against the algorithmic flops and bytes of the "
+                     "method's Liouvillian applications (pruned FFTs, contractions, pointwise "
+                     "products; response vectors, orbitals, projectors)",
+            "flops_per_step": alg_flops, "alg_bytes_per_step": alg_bytes,
+            "achieved_gbs": alg_bytes / step_s / 1e9, "hbm_peak_gbs": hbm,
+            "frac_hbm": alg_bytes / step_s / 1e9 / hbm, "hbm_peak_source": peak_src,
+            "design_bytes_per_step": design_bytes_step,
+            "design_over_alg_bytes": design_bytes_step / alg_bytes,
+            "traffic": None,
+            "dominant_kernel": {
+                "stage": top, "bound": "hbm",
+                "achieved_gbs": bytes_launch / per_launch_s / 1e9,
+                "frac": bytes_launch / per_launch_s / 1e9 / hbm,
+                "design_bytes_per_launch": bytes_launch, "launches": nl,
+                "traffic": ncu_traffic(args, top), "traffic_unit": "bytes per launch"}},
         "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
         "stages_fp64_ms_per_step": {k: round(v["ms"] / fp64_steps, 4) for k, v in prof64.items()
                                     if v["launches"]},
