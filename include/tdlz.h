@@ -125,8 +125,12 @@ typedef struct {
   double *z;       /* [nchain][3][nsteps] complex */
   double *n0;      /* [nchain] start-vector norm in the flavour's metric */
   double *wk;      /* [nchain] k weight w */
-  int *steps_done; /* [nchain] */
-  int *status;     /* [nchain] tdlz_status of each chain */
+  int *steps_done; /* [nchain] steps whose alpha and z are valid: a chain that breaks
+                      down (TDLZ_ERR_BREAKDOWN: beta of the next step below the
+                      tolerance) keeps the step it broke down on; one whose alpha or z
+                      came out non-finite (TDLZ_ERR_NUMERIC) ends before that step */
+  int *status;     /* [nchain] tdlz_status of each chain; a stopped chain leaves the
+                      other chains of the set running */
 } tdlz_lanczos_result;
 
 typedef struct {
@@ -223,7 +227,10 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
  * held by every GPU that loads the library until the process exits; frequencies
  * are processed in chunks that fit it.  Rejected with TDLZ_ERR_ARG (nothing
  * launched): 4 * nchain * nsteps complex rows above the scratch, i.e.
- * nchain * nsteps > TDLZ_NOALLOC_SCRATCH_MB * 2^20 / 64.  The first call on a
+ * nchain * nsteps > TDLZ_NOALLOC_SCRATCH_MB * 2^20 / 64, and grids longer than
+ * 2^24 frequencies.  The per-chain step counts dev_coeffs->steps stay on the device,
+ * so they are not checked: values outside [0, nsteps] are clamped to that range
+ * (tdlz_spectrum, which receives them on the host, rejects them).  The first call on a
  * device looks up the scratch's device address (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture.  Every call on a
  * device shares the one array and leaves its contents behind (each call writes

@@ -81,6 +81,16 @@ tdlz_status tdlz_create(tdlz_ctx **out, int device, void *cuda_stream) {
   const char *at = std::getenv("TDLZ_AUTOTUNE");
   ctx->c.tuner.on = !(at && at[0] == '0');
   ctx->c.tuner.device = device;
+  // test hook: TDLZ_TEST_INJECT_TC_TIMEOUT=n makes the next n completed mbarrier waits of
+  // the tensor-core GEMMs report expiry (the abort and reporting path, no real timeout)
+  if (const char *inj = std::getenv("TDLZ_TEST_INJECT_TC_TIMEOUT")) {
+    try {
+      tdlz::tc_gemm_inject_timeout(std::atoi(inj));
+    } catch (const tdlz::Error &) {
+      delete ctx;
+      return TDLZ_ERR_CUDA;
+    }
+  }
   if (cuda_stream) {
     ctx->c.stream = (cudaStream_t)cuda_stream;
   } else {

@@ -174,7 +174,7 @@ __global__ void scalar_a_kernel(const double2 *partial, int nblk, ChainScalars *
   if (!finite2(alpha) || !finite2(d[1]) || !finite2(d[2]) || !finite2(d[3])) {
     cs->status = TDLZ_ERR_NUMERIC;
     cs->stopped = 1;
-    cs->steps_done = j + 1;
+    cs->steps_done = j;  // step j has no valid alpha or z: the chain ends before it
   }
 }
 

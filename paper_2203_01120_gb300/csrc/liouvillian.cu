@@ -920,6 +920,34 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   size_t brb = (size_t)s.br_elems() * sizeof(double2);
   up(d.ukq, ukq_int.data(), brb);
   up(s.coeff_k, gs->coeff_k, brb);
+  // the occupied states at k and k+q of each side must be orthonormal (U^+ U = 1): the
+  // conduction projector P_c = 1 - sum |U><U| and the pseudo-Hermiticity of L rest on it
+  {
+    const int batch = 2 * nk;
+    const long long bstride = (long long)nb * 2 * npwx;
+    DevBuf gram, gpart;
+    gram.alloc((size_t)batch * nb * nb * sizeof(double2));
+    gpart.alloc((size_t)32 * batch * nb * nb * sizeof(double2));
+    std::vector<double> g((size_t)batch * nb * nb * 2);
+    double err = 0.0;
+    for (const DevBuf *u : {&d.ukq, &s.coeff_k}) {
+      gemm_tn<double>(ctx, gpart, u->as<double2>(), 2LL * npwx, bstride, batch,
+                      u->as<double2>(), 2LL * npwx, bstride, gram.as<double2>(),
+                      (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
+      TDLZ_CUDA_TRY(cudaMemcpyAsync(g.data(), gram.p, g.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+      TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int b = 0; b < batch; ++b)
+        for (int m = 0; m < nb; ++m)
+          for (int n = 0; n < nb; ++n) {
+            const double *e = g.data() + 2 * (((size_t)b * nb + m) * nb + n);
+            err = std::max(err, std::hypot(e[0] - (m == n ? 1.0 : 0.0), e[1]));
+          }
+    }
+    TDLZ_REQUIRE(err <= 1e-6, TDLZ_ERR_ARG,
+                 "occupied states are not orthonormal (max |U^+U - 1| = " + std::to_string(err) +
+                     " > 1e-6)");
+  }
   if (np_ > 0) {
     up(d.beta, beta_int.data(), (size_t)nk * np_ * npwx * sizeof(double2));
     up(d.dnl, gs->dnl, (size_t)4 * np_ * np_ * sizeof(double2));

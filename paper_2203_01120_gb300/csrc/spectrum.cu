@@ -10,23 +10,9 @@
 #include <vector>
 
 #include "spectrum.cuh"
+#include "spectrum_solve.cuh"
 
 namespace tdlz {
-
-namespace {
-
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  // a / b with scaling (Smith's method)
-  if (fabs(b.x) >= fabs(b.y)) {
-    double r = b.y / b.x, den = b.x + b.y * r;
-    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
-  }
-  double r = b.x / b.y, den = b.x * r + b.y;
-  return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
-}
-__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
-
-}  // namespace
 
 __global__ void spectrum_kernel(SpecArgs a) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -86,76 +72,13 @@ __global__ void spectrum_kernel(SpecArgs a) {
         den.x -= bg.x * g.x - bg.y * g.y;
         den.y -= bg.x * g.y + bg.y * g.x;
       }
-      g = cdiv(make_double2(1.0, 0.0), den);
+      g = spec_cdiv(make_double2(1.0, 0.0), den);
     }
     double2 bg = make_double2(be[m - 1] * ga[m - 1].x, be[m - 1] * ga[m - 1].y);
     tail = make_double2(bg.x * g.x - bg.y * g.y, bg.x * g.y + bg.y * g.x);
   }
-  // scratch rows (final d, du, du2, b) at [j][tid]
-  double2 *sd = a.scratch, *sdu = a.scratch + (long long)a.cap * nthr,
-          *sdu2 = a.scratch + 2LL * a.cap * nthr, *sb = a.scratch + 3LL * a.cap * nthr;
-  // A = zw - T: d_j = zw - alpha_j, dl_j = -beta_j (A[j+1][j]), du_j = -gamma_j (A[j][j+1])
-  double2 d = make_double2(zw.x - al[0].x, zw.y - al[0].y);
-  if (m == 1) d = make_double2(d.x - tail.x, d.y - tail.y);
-  double2 du = m > 1 ? make_double2(-ga[0].x, -ga[0].y) : make_double2(0, 0);
-  double2 b = make_double2(1.0, 0.0);
-  for (int i = 0; i < m - 1; ++i) {
-    double2 dl = make_double2(-be[i], 0.0);
-    double2 dn = make_double2(zw.x - al[i + 1].x, zw.y - al[i + 1].y);  // d_{i+1}
-    if (i + 1 == m - 1) dn = make_double2(dn.x - tail.x, dn.y - tail.y);
-    double2 dun = (i + 1 < m - 1) ? make_double2(-ga[i + 1].x, -ga[i + 1].y) : make_double2(0, 0);
-    double2 bn = make_double2(0, 0);
-    double2 du2 = make_double2(0, 0);
-    if (cabs2(d) >= cabs2(dl)) {
-      double2 f = cdiv(dl, d);
-      dn = make_double2(dn.x - (f.x * du.x - f.y * du.y), dn.y - (f.x * du.y + f.y * du.x));
-      bn = make_double2(bn.x - (f.x * b.x - f.y * b.y), bn.y - (f.x * b.y + f.y * b.x));
-    } else {
-      double2 f = cdiv(d, dl);
-      double2 tmp = dn;
-      double2 nd = dl;
-      dn = make_double2(du.x - (f.x * tmp.x - f.y * tmp.y), du.y - (f.x * tmp.y + f.y * tmp.x));
-      du2 = dun;
-      dun = make_double2(-(f.x * du2.x - f.y * du2.y), -(f.x * du2.y + f.y * du2.x));
-      du = tmp;
-      d = nd;
-      double2 tb = b;
-      b = bn;  // = 0
-      bn = make_double2(tb.x - (f.x * b.x - f.y * b.y), tb.y - (f.x * b.y + f.y * b.x));
-    }
-    long long o = (long long)i * nthr + tid;
-    sd[o] = d;
-    sdu[o] = du;
-    sdu2[o] = du2;
-    sb[o] = b;
-    d = dn;
-    du = dun;
-    b = bn;
-  }
-  {
-    long long o = (long long)(m - 1) * nthr + tid;
-    sd[o] = d;
-    sdu[o] = make_double2(0, 0);
-    sdu2[o] = make_double2(0, 0);
-    sb[o] = b;
-  }
-  // back substitution with chi accumulation
-  double2 x1 = make_double2(0, 0), x2 = make_double2(0, 0);  // x_{i+1}, x_{i+2}
-  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-  for (int i = m - 1; i >= 0; --i) {
-    long long o = (long long)i * nthr + tid;
-    double2 bi = sb[o], dui = sdu[o], du2i = sdu2[o];
-    double2 num = make_double2(bi.x - (dui.x * x1.x - dui.y * x1.y) - (du2i.x * x2.x - du2i.y * x2.y),
-                               bi.y - (dui.x * x1.y + dui.y * x1.x) - (du2i.x * x2.y + du2i.y * x2.x));
-    double2 xi = cdiv(num, sd[o]);
-    for (int l = 0; l < 3; ++l) {
-      double2 zv = zz[(long long)l * a.cap + i];
-      acc[l].x += zv.x * xi.x + zv.y * xi.y;
-      acc[l].y += zv.x * xi.y - zv.y * xi.x;
-    }
-    x2 = x1;
-    x1 = xi;
-  }
+  double2 acc[3];
+  tridiag_chi(m, a.cap, al, be, ga, zz, zw, tail, a.scratch, nthr, tid, acc);
   double s = a.wk[c] * a.n0[c];
   for (int l = 0; l < 3; ++l)
     out[(long long)l * a.nomega] = make_double2(s * acc[l].x, s * acc[l].y);

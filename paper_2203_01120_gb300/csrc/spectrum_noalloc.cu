@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "engine.cuh"
+#include "spectrum_solve.cuh"
 
 namespace tdlz {
 
@@ -23,15 +24,6 @@ static __device__ __align__(256) double2 g_spec_scratch[kNoallocScratchBytes / s
 std::mutex g_mu;
 double2 *g_scratch_ptr[kMaxDevices] = {nullptr};
 
-__device__ __forceinline__ double2 nd_cdiv(double2 a, double2 b) {
-  if (fabs(b.x) >= fabs(b.y)) {
-    double r = b.y / b.x, den = b.x + b.y * r;
-    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
-  }
-  double r = b.x / b.y, den = b.x * r + b.y;
-  return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
-}
-
 // One thread per (chain, omega) of the chunk [w0, w0 + nw); rows stored at
 // scratch[(q * cap + i) * nthr + tid] for q = d, du, du2, b.
 __global__ void spectrum_noalloc_kernel(int nchain, int nomega, int cap, const int *steps,
@@ -44,7 +36,7 @@ __global__ void spectrum_noalloc_kernel(int nchain, int nomega, int cap, const i
   if (tid >= nthr) return;
   int c = (int)(tid / nw);
   int iw = w0 + (int)(tid - (long long)c * nw);
-  int m = steps[c];
+  int m = steps[c];  // read on the device: clamped to [0, cap]
   if (m > cap) m = cap;
   double2 *out = chi + ((long long)c * 3) * nomega + iw;
   if (m <= 0) {
@@ -55,63 +47,9 @@ __global__ void spectrum_noalloc_kernel(int nchain, int nomega, int cap, const i
   const double *be = beta + (long long)c * cap;
   const double2 *ga = gamma + (long long)c * cap;
   const double2 *zz = z + (long long)c * 3 * cap;
-  double2 zw = make_double2(start + step * iw, eta);
-  double2 *sd = scratch, *sdu = scratch + (long long)cap * nthr,
-          *sdu2 = scratch + 2LL * cap * nthr, *sb = scratch + 3LL * cap * nthr;
-  double2 d = make_double2(zw.x - al[0].x, zw.y - al[0].y);
-  double2 du = m > 1 ? make_double2(-ga[0].x, -ga[0].y) : make_double2(0, 0);
-  double2 b = make_double2(1.0, 0.0);
-  for (int i = 0; i < m - 1; ++i) {
-    double2 dl = make_double2(-be[i], 0.0);
-    double2 dn = make_double2(zw.x - al[i + 1].x, zw.y - al[i + 1].y);
-    double2 dun = (i + 1 < m - 1) ? make_double2(-ga[i + 1].x, -ga[i + 1].y) : make_double2(0, 0);
-    double2 bn = make_double2(0, 0), du2 = make_double2(0, 0);
-    if (hypot(d.x, d.y) >= hypot(dl.x, dl.y)) {  // keep row i as pivot row
-      double2 f = nd_cdiv(dl, d);
-      dn = make_double2(dn.x - (f.x * du.x - f.y * du.y), dn.y - (f.x * du.y + f.y * du.x));
-      bn = make_double2(-(f.x * b.x - f.y * b.y), -(f.x * b.y + f.y * b.x));
-    } else {  // swap rows i and i+1 (row i+1 becomes the pivot row)
-      double2 f = nd_cdiv(d, dl);
-      double2 old_dn = dn;
-      dn = make_double2(du.x - (f.x * old_dn.x - f.y * old_dn.y),
-                        du.y - (f.x * old_dn.y + f.y * old_dn.x));
-      du2 = dun;
-      dun = make_double2(-(f.x * du2.x - f.y * du2.y), -(f.x * du2.y + f.y * du2.x));
-      du = old_dn;
-      d = dl;
-      bn = b;  // b_{i+1} was zero before the swap
-      b = make_double2(0, 0);
-    }
-    long long o = (long long)i * nthr + tid;
-    sd[o] = d;
-    sdu[o] = du;
-    sdu2[o] = du2;
-    sb[o] = b;
-    d = dn;
-    du = dun;
-    b = bn;
-  }
-  long long o = (long long)(m - 1) * nthr + tid;
-  sd[o] = d;
-  sdu[o] = make_double2(0, 0);
-  sdu2[o] = make_double2(0, 0);
-  sb[o] = b;
-  double2 x1 = make_double2(0, 0), x2 = make_double2(0, 0);
-  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-  for (int i = m - 1; i >= 0; --i) {
-    long long oi = (long long)i * nthr + tid;
-    double2 bi = sb[oi], dui = sdu[oi], du2i = sdu2[oi];
-    double2 num = make_double2(bi.x - (dui.x * x1.x - dui.y * x1.y) - (du2i.x * x2.x - du2i.y * x2.y),
-                               bi.y - (dui.x * x1.y + dui.y * x1.x) - (du2i.x * x2.y + du2i.y * x2.x));
-    double2 xi = nd_cdiv(num, sd[oi]);
-    for (int l = 0; l < 3; ++l) {
-      double2 zv = zz[(long long)l * cap + i];
-      acc[l].x += zv.x * xi.x + zv.y * xi.y;
-      acc[l].y += zv.x * xi.y - zv.y * xi.x;
-    }
-    x2 = x1;
-    x1 = xi;
-  }
+  double2 acc[3];
+  tridiag_chi(m, cap, al, be, ga, zz, make_double2(start + step * iw, eta), make_double2(0, 0),
+              scratch, nthr, tid, acc);
   double s = wk[c] * n0[c];
   for (int l = 0; l < 3; ++l) out[(long long)l * nomega] = make_double2(s * acc[l].x, s * acc[l].y);
 }
@@ -147,6 +85,7 @@ void spectrum_noalloc(Context &ctx, const tdlz_coeffs *c, const tdlz_spectrum_pa
   long long nw = (long long)std::floor((sp->end - sp->start) / sp->step + 0.5) + 1;
   TDLZ_REQUIRE(nw == nomega, TDLZ_ERR_ARG,
                "nomega does not match the frequency grid (query it with tdlz_spectrum, chi = NULL)");
+  TDLZ_REQUIRE(nw <= (1LL << 24), TDLZ_ERR_ARG, "at most 2^24 frequencies");
   // every frequency needs 4 complex rows of length nsteps per chain
   const long long per_omega = 4LL * c->nsteps * c->nchain;  // double2 elements
   const long long cap_elems = (long long)(kNoallocScratchBytes / sizeof(double2));

@@ -41,6 +41,7 @@ constexpr int kMaxA = 64 / kRowStep;            // A rows per thread (M <= 64)
 constexpr int kMaxB = 256 / kRowStep;           // B rows per thread (N tile <= 256)
 
 __device__ int g_tc_timeout = 0;
+__device__ int g_tc_inject = 0;  // test hook: expiries to report after real completion
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,7 +73,7 @@ __device__ __forceinline__ uint32_t tile_off(int r, int c, uint32_t lbo) {
   return (uint32_t)c * lbo + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_raw(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
   for (long long it = 0; it < kSpinLimit; ++it) {
     asm volatile(
@@ -84,6 +85,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+// Bounded wait for the phase `parity` of barrier `bar`.  A pending test injection
+// (g_tc_inject > 0, set on the host) makes one completed wait report expiry: the
+// abort path then runs with every MMA of the CTA finished.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (!mbar_wait_raw(bar, parity)) return false;
+  int v = *(volatile int *)&g_tc_inject;
+  while (v > 0) {
+    const int old = atomicCAS(&g_tc_inject, v, v - 1);
+    if (old == v) return false;
+    v = old;
+  }
+  return true;
+}
+
+// End of the MMA loop of a CTA that committed its first `committed` K tiles (all of
+// them, or those before an expired wait at tile abort_it): wait for the last commit,
+// which covers every MMA issued before it, so that TMEM is neither read nor released
+// while an MMA may still write it.  Without an earlier expiry the wait is the drain
+// and may itself report expiry; after one, the wait ignores test injections.  If the
+// GPU really stopped answering for the whole bounded wait the CTA releases TMEM
+// anyway (the context is then unusable: the host reports TDLZ_ERR_TIMEOUT).
+__device__ __forceinline__ void quiesce(uint64_t *mbar, int &abort_flag, int abort_it,
+                                        int nloc) {
+  const int committed = abort_flag ? abort_it : nloc;
+  if (committed > 0) {
+    const int last = committed - 1;
+    const uint32_t bar = smem_u32(&mbar[last & 1]), par = (uint32_t)((last >> 1) & 1);
+    if (!abort_flag && !mbar_wait(bar, par)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) mbar_wait_raw(bar, par);
+  }
+  __syncthreads();
 }
 
 struct TcArgs {
@@ -105,7 +140,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, abort_it;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = g.nt;
   const uint32_t lboA = 16 * 128, lboB = (uint32_t)(nt / 8) * 128;
@@ -126,6 +161,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
+    abort_it = nloc;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -188,7 +224,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
     const int s = it & 1;
     // tile it's loads are in flight while the MMAs of tile it-2 release stage s
     if (it >= 2) {
-      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) {
+        abort_flag = 1;
+        abort_it = it;
+      }
     }
     __syncthreads();
     if (abort_flag) break;
@@ -247,12 +286,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
               smem_u32(&mbar[s])));
     }
   }
-  // drain: the last commit covers every MMA issued before it
-  if (nloc > 0 && !abort_flag) {
-    const int last = nloc - 1;
-    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_flag = 1;
-  }
-  __syncthreads();
+  quiesce(mbar, abort_flag, abort_it, nloc);
   asm volatile("tcgen05.fence::after_thread_sync;");
   const bool ok = !abort_flag && nloc > 0;
   if (!ok && tid == 0 && abort_flag) atomicExch(&g_tc_timeout, 1);
@@ -262,14 +296,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
   const int row = 32 * quarter + (tid & 31);
   float *out = g.part + ((((long long)z * gridDim.y + a) * g.ntiles + tile) * 128 + row) * nt;
   for (int c0 = 8 * (warp >> 2); c0 < nt; c0 += 16) {
-    uint32_t r[8];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (ok) {  // TMEM is read only after the last commit's barrier completed
+      const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+    }
     if (row < 2 * g.M) {
       float4 *o = reinterpret_cast<float4 *>(out + c0);
       if (ok) {
@@ -345,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, abort_it;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ct = blockIdx.x;  // column tile
   const long long b = blockIdx.y;   // batch
@@ -361,6 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
+    abort_it = g.nkt;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -413,7 +450,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
   for (int it = 0; it < g.nkt; ++it) {
     const int s = it & 1;
     if (it >= 2) {
-      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) abort_flag = 1;
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) {
+        abort_flag = 1;
+        abort_it = it;
+      }
     }
     __syncthreads();
     if (abort_flag) break;
@@ -471,11 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
               smem_u32(&mbar[s])));
     }
   }
-  if (g.nkt > 0 && !abort_flag) {
-    const int last = g.nkt - 1;
-    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_flag = 1;
-  }
-  __syncthreads();
+  quiesce(mbar, abort_flag, abort_it, g.nkt);
   asm volatile("tcgen05.fence::after_thread_sync;");
   const bool ok = !abort_flag;
   if (abort_flag && tid == 0) atomicExch(&g_tc_timeout, 1);
@@ -493,6 +529,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       iv[u] = (nv && r0 + u < g.R) ? inb[(long long)(r0 + u) * g.ldo] : make_float2(0.f, 0.f);
+    if (!ok) break;  // TMEM is read only after the last commit's barrier completed
     uint32_t v[16];
     const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0;
     asm volatile(
@@ -608,6 +645,10 @@ bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long
   tc_gemm_nn_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(g);
   TDLZ_LAUNCH_CHECK();
   return true;
+}
+
+void tc_gemm_inject_timeout(int n) {
+  TDLZ_CUDA_TRY(cudaMemcpyToSymbol(g_tc_inject, &n, sizeof(int)));
 }
 
 void tc_gemm_check() {

@@ -27,4 +27,9 @@ bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long
 // mbarrier wait since the last check.  Synchronous.
 void tc_gemm_check();
 
+// Test hook (TDLZ_TEST_INJECT_TC_TIMEOUT=n at context creation): the next n bounded
+// mbarrier waits that complete report expiry instead, so that the abort path runs (and
+// is reported) with every MMA of the CTA finished; no wait is cut short.
+void tc_gemm_inject_timeout(int n);
+
 }  // namespace tdlz

@@ -49,6 +49,61 @@ def test_noalloc_matches_allocating_entry_point(setup):
         assert err <= 1e-12, (call, err)
 
 
+def test_noalloc_matches_across_frequency_chunks(setup):
+    """Coefficient arrays padded to 20000 steps (40 computed): the scratch then holds
+    only 13 frequencies per chunk, so the 4001-point grid runs in many chunks, the
+    last one shorter; every chunk must equal the allocating entry point."""
+    torch, ctx, coeffs = setup
+    cap = 20000
+    padded = dict(coeffs)
+    for key in ("alpha", "beta", "gamma"):
+        a = np.zeros((2, cap), dtype=coeffs[key].dtype)
+        a[:, :coeffs[key].shape[1]] = coeffs[key]
+        padded[key] = a
+    zpad = np.zeros((2, 3, cap), dtype=coeffs["z"].dtype)
+    zpad[:, :, :coeffs["z"].shape[2]] = coeffs["z"]
+    padded["z"] = zpad
+    grid = (0.0, 2000.0, 0.5, 10.0, 1)
+    ref = ctx.spectrum(padded, *grid)
+    nw = ref.shape[-1]
+    assert (32 * 2 ** 20 // 16) // (4 * cap * 2) < nw  # several chunks
+    dev = _to_device(torch, padded)
+    chi = torch.full((2, 3, nw), float("nan"), dtype=torch.complex128, device="cuda")
+    ctx.spectrum_noalloc(dev, *grid, chi)
+    ctx.synchronize()
+    got = chi.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_noalloc_allocates_nothing(setup):
+    """A call recorded in a CUDA graph in global capture mode (any allocation or
+    synchronisation inside it would invalidate the capture) and replayed gives the
+    same chi as an eager call."""
+    torch, ctx0, coeffs = setup
+    from paper_2203_01120_gb300 import Context
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream.cuda_stream)
+    try:
+        grid = (0.0, 2000.0, 0.5, 10.0, 1)
+        ref = ctx0.spectrum(coeffs, *grid)
+        nw = ref.shape[-1]
+        dev = _to_device(torch, coeffs)
+        chi = torch.zeros((2, 3, nw), dtype=torch.complex128, device="cuda")
+        ctx.spectrum_noalloc(dev, *grid, chi)  # first call on the device: before capture
+        ctx.synchronize()
+        chi.zero_()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="global"):
+            ctx.spectrum_noalloc(dev, *grid, chi)
+        g.replay()
+        torch.cuda.synchronize()
+        got = chi.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    finally:
+        ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(setup):
     torch, ctx, coeffs = setup
     from paper_2203_01120_gb300 import TdlzError
