@@ -510,11 +510,13 @@ def sphere_sticks_planes(gs):
     return nsm, npm
 
 
-def chi_column_errors(c32, c64):
-    """Per chi column mu: max over lambda of ||chi32 - chi64||_2 / ||chi64[mu][mu]||_2."""
+def chi_column_errors(c32, c64, mus=None):
+    """Per chi column mu: max over lambda of ||chi32 - chi64||_2 / ||chi64[mu][mu]||_2
+    (row i of the arrays is the chain of column mus[i], default i)."""
     import numpy as np
-    return [float(np.linalg.norm(c32[i] - c64[i], axis=1).max() / np.linalg.norm(c64[i][i]))
-            for i in range(len(c64))]
+    mus = list(range(len(c64))) if mus is None else mus
+    return [float(np.linalg.norm(c32[i] - c64[i], axis=1).max() / np.linalg.norm(c64[i][mu]))
+            for i, mu in enumerate(mus)]
 
 
 def run_tdlz(args):
@@ -530,7 +532,7 @@ def run_tdlz(args):
     gs = make_workload(args.config, args.tol, args.bundle, args.states)
     if args.kpoints:  # profiling captures only: the first k points of the workload
         gs = sample_bundle(gs, args.kpoints)
-    chi_steps = args.chi_steps if args.config in ("C2", "C4") else min(args.chi_steps, 20)
+    chi_steps = args.chi_steps if args.config in ("C1", "C2") else min(args.chi_steps, 10)
     # replicas: every rank runs the chi columns mus (the paper's ipol = 4: x, y, z)
     mus = list(range(args.chains))
     stream = torch.cuda.Stream(device=local)
@@ -567,7 +569,7 @@ def run_tdlz(args):
     flavors = {args.flavor: {"value": len(mus) * args.steps / wall_mixed, "unit": "steps/s",
                              "ms_per_step": 1000 * wall_mixed / args.steps,
                              "l_applications_per_step": len(mus) * (2 if args.flavor == "nh" else 1)}}
-    if not args.mixed_only:
+    if not args.mixed_only and args.config in ("C1", "C2"):
         for fl in ("nh", "ph"):
             if fl in flavors:
                 continue
@@ -585,14 +587,19 @@ def run_tdlz(args):
         sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(
             ctx, q, mus, args.flavor, TDLZ_FP64, 1, fp64_steps, stream, profile=True)
         # ------------------------------------------------ chi error mixed vs FP64
-        r64 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_FP64)
-        r32 = ctx.lanczos_run([q] * len(mus), mus, m, args.flavor, TDLZ_MIXED)
-        chi = {"steps": m, "omega_mev": [0.0, 100.0, 0.1], "eta_mev": 10.0, "tolerance": 1e-4,
+        # C2: the timed chains; larger cells (shape-only occupied states, where the
+        # J-metric start vector has a J-norm ~1e-3 of its norm and the PH recursion is
+        # ill-conditioned from its first steps) one NH chain over a short prefix
+        chi_fl, chi_mus = (args.flavor, mus) if args.config in ("C1", "C2") else ("nh", [0])
+        r64 = ctx.lanczos_run([q] * len(chi_mus), chi_mus, m, chi_fl, TDLZ_FP64)
+        r32 = ctx.lanczos_run([q] * len(chi_mus), chi_mus, m, chi_fl, TDLZ_MIXED)
+        chi = {"steps": m, "flavor": chi_fl, "chains": chi_mus, "omega_mev": [0.0, 100.0, 0.1],
+               "eta_mev": 10.0, "tolerance": 1e-4,
                "norm": "per column mu: max over lambda ||chi_mixed - chi_fp64|| / ||chi_fp64[mu][mu]||"}
         for mm in sorted({m, min(m, 100)}):
             c64 = ctx.spectrum(r64, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
             c32 = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
-            chi[f"rel_err_{mm}"] = chi_column_errors(c32, c64)
+            chi[f"rel_err_{mm}"] = chi_column_errors(c32, c64, chi_mus)
         chi["status"] = [int(v) for v in r32["status"]] + [int(v) for v in r64["status"]]
         # conditioning probe: the same mixed chains through the other real-space path
         # (same operator and precision, different rounding order); where the two FP32
@@ -613,7 +620,7 @@ def run_tdlz(args):
     ctx.close()
     # cuFFT on the same batch as one pass: full box, and driven the same pruned way
     cufft = None
-    if not args.kpoints and not args.mixed_only:
+    if not args.kpoints and not args.mixed_only and args.config in ("C1", "C2"):
         rows = len(mus) * (2 if args.flavor == "nh" else 1) * 4 * gs.nk * gs.nocc
         fft = tuple(int(n) for n in gs.fft)
         cufft = {"full_box": cufft_baseline(rows, fft, local)}
@@ -707,6 +714,141 @@ def run_tdlz(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5(args):
+    """The batched form (C5): six q-points m/16 (2pi/a), m = 1..6, along x of the
+    CrI3-shaped cell on a 4x4 k grid, each with its own cutoff (10000-13000 plane waves per
+    spinor component), three chains (mu = x, y, z) on each: 18 chains in one chain set,
+    one group per q-slot, advanced together and replayed from one captured graph, mixed
+    precision.  Occupied states random orthonormal (the cost of a step does not depend
+    on them); q-slots loaded for mixed precision only (the FP64 orbitals released)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2203_01120_gb300 import TDLZ_MIXED, Context, build_ext
+    from synth import make_ground_state
+    from synth.configs import c5_ecut
+    build_ext.build()
+    nq = 6
+    t = time.time()
+    bundles = [make_ground_state("C5", q_2pi_a=(m / 16.0, 0.0, 0.0), ecut=c5_ecut(m, nq),
+                                 solver="random") for m in range(1, nq + 1)]
+    log(f"[bench] C5: {nq} shape-only bundles ({time.time() - t:.1f} s), npw_kq "
+        f"{[int(b.npw_kq.mean()) for b in bundles]}")
+    stream = torch.cuda.Stream(device=local)
+    ctx = Context(local, stream=stream.cuda_stream)
+    os.environ["TDLZ_MIXED_ONLY"] = "1"
+    try:
+        t0 = time.perf_counter()
+        qs = [ctx.load_ground_state(b) for b in bundles]
+        t1 = time.perf_counter()
+    finally:
+        del os.environ["TDLZ_MIXED_ONLY"]
+    slots = [q for q in qs for _ in range(3)]
+    mus = [mu for _ in qs for mu in range(3)]
+    nch = len(mus)
+    # e2e: the loads above + chain start + K steps + coefficients to the host
+    ch = ctx.chain_create(slots, mus, args.steps, args.flavor, TDLZ_MIXED)
+    ctx.synchronize()
+    t2 = time.perf_counter()
+    ch.advance(args.steps)
+    res_e2e = ch.read()
+    e2e_wall = time.perf_counter() - t0
+    ch.close()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ch = ctx.chain_create(slots, mus, args.warmup + args.steps + 1, args.flavor, TDLZ_MIXED)
+    ch.advance(args.warmup)
+    ctx.synchronize()
+    l0 = ctx.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ch.advance(args.steps)
+    ev1.record(stream)
+    ctx.synchronize()
+    wall = ev0.elapsed_time(ev1) / 1000.0
+    launches = ctx.launch_count() - l0
+    clocks = clk.finish()
+    wall = max_over_ranks(wall, "cuda")
+    res = ch.read()
+    ch.close()
+    ctx.profile(True)
+    chp = ctx.chain_create(slots, mus, args.steps + 2, args.flavor, TDLZ_MIXED)
+    chp.advance(1)
+    ctx.profile(False)
+    ctx.profile(True)
+    chp.advance(args.steps)
+    ctx.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    chp.close()
+    ctx.close()
+    if rank != 0:
+        return
+    step_s = wall / args.steps
+    alg_b = alg_f = 0.0
+    for b in bundles:
+        bb, ff = algorithmic_work(b, args.flavor, 3, 8)
+        alg_b, alg_f = alg_b + bb, alg_f + ff
+    peak32, src32 = fp32_peak_tflops(local)
+    hbm, peak_src = measured_peaks()
+    stages = {k: v for k, v in prof.items() if v["launches"] > 0 and v["ms"] > 0}
+    cores, model = cpu_info()
+    cpu = None
+    if not args.no_cpu_baseline:
+        per, el, nks = oracle_step_time(bundles[0], 1, args.flavor, nk_sample=1)
+        cpu = {"value": 1.0 / per, "unit": "chain-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle Lanczos step ({args.flavor}) of the q = 1/16 chain "
+                         f"restricted to k point 0 of 16, {el:.1f} s, scaled x16 (cost linear "
+                         "in k; the other q-points have 0.9-1.2 times its plane waves)",
+               "cpu": model}
+    bundle_bytes = sum(sum(int(np.asarray(getattr(b, k)).nbytes) for k in (
+        "kpts", "wk", "npw_k", "npw_kq", "miller_k", "miller_kq", "evals", "coeff_k", "coeff_kq",
+        "vloc", "bfield", "n0", "m0", "beta_kq", "dnl")) for b in bundles)
+    line = {
+        "metric": METRIC, "value": whole_job_rate(world, nch, args.steps, wall),
+        "l_applications_per_s": whole_job_rate(world, nch, args.steps, wall)
+        * (2 if args.flavor == "nh" else 1),
+        "unit": "chain-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * step_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "C5: batched form, hexagonal a=13 c=38 bohr, FFT 45x45x144, 4x4 k, "
+                               "Nocc=70, 8 atoms x 8 KB projectors with SOC, q = m/16 2pi/a "
+                               "(m = 1..6) with 10000-13000 PW per component, 3 chains per q",
+                   "flavor": args.flavor, "precision": "mixed", "chains_per_gpu": nch,
+                   "q_points": nq, "parallelism": f"replicas{world}",
+                   "npw_kq_mean_per_q": [int(b.npw_kq.mean()) for b in bundles],
+                   "occupied_states": "random orthonormal (shape only)",
+                   "ms_per_step_is": "one step of all 18 chains (6 q-slot groups, one graph)",
+                   "l2": "inputs larger than L2"},
+        "roofline": {
+            "bound": "alu", "achieved": alg_f / step_s / 1e12, "peak": peak32, "unit": "TFLOP/s",
+            "frac": alg_f / step_s / 1e12 / peak32, "peak_source": src32,
+            "scope": "the whole batched step against the algorithmic flops and bytes of its "
+                     "Liouvillian applications",
+            "flops_per_step": alg_f, "alg_bytes_per_step": alg_b,
+            "achieved_gbs": alg_b / step_s / 1e9, "hbm_peak_gbs": hbm,
+            "frac_hbm": alg_b / step_s / 1e9 / hbm, "hbm_peak_source": peak_src, "traffic": None},
+        "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
+        "clocks": clocks, "gpu_launches": launches,
+        "e2e": {"value": nch * args.steps / e2e_wall, "unit": "chain-steps/s",
+                "h2d_bytes_per_step": bundle_bytes / args.steps,
+                "d2h_bytes_per_step": nch * args.steps * (16 * 2 + 8 + 16 * 3) / args.steps,
+                "what": "load_ground_state of the 6 host bundles + chain set of K mixed steps + "
+                        "coefficients to host, through the C ABI",
+                "load_s": t1 - t0, "chain_start_s": t2 - t1},
+        "cpu_baseline": cpu,
+        "status": [int(v) for v in res["status"]],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_apply(args):
     """Small, self-contained case for profilers: a shape-only bundle of the config
     (random orthonormal occupied states, no diagonalisation) and a few Liouvillian
@@ -746,6 +888,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "C5":
+        run_c5(args)
     else:
         run_tdlz(args)
 

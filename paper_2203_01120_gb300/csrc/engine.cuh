@@ -127,6 +127,9 @@ struct QSlot {
   // the Liouvillian of each precision runs the fused plane stages (planes.cu); otherwise
   // the staged pipeline with real-space grids in HBM (pipeline.cu)
   bool planes32 = false, planes64 = false;
+  // loaded for mixed precision only (TDLZ_MIXED_ONLY=1): the FP32 data is built at load
+  // and the FP64 real-space orbitals are released; FP64 applications are refused
+  bool mixed_only = false;
   bool tensor_gemm = true;  // FP32 V_NL / P_c reductions and updates on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;

@@ -626,7 +626,7 @@ void alloc_workspace(QSlot &s, int nvec) {
   w.rho.alloc(nv * 4 * (size_t)s.nr * c);
   w.hgrid.alloc(nv * (size_t)s.nr * c);
   w.h.alloc(nv * (size_t)s.br_elems() * c);
-  w.xin.alloc(nv * (size_t)s.br_elems() * c);
+  w.xin.reset();  // the adjoint's input copy: allocated on its first use
   size_t batch = nv * 2 * s.nk;
   w.proj.alloc(batch * s.nproj * 2 * s.nb * c + c);
   w.dmix.alloc(batch * s.nproj * 2 * s.nb * c + c);
@@ -1015,6 +1015,16 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     TDLZ_LAUNCH_CHECK();
   }
   d.ready = true;
+  // TDLZ_MIXED_ONLY=1: build the FP32 data now and release the FP64 real-space orbitals
+  // (the largest FP64 array), for runs of many q-slots in mixed precision
+  const char *mo = std::getenv("TDLZ_MIXED_ONLY");
+  if (mo && mo[0] == '1') {
+    ensure_precision<float>(ctx, s);
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+    d.us.reset();
+    d.ur.reset();
+    s.mixed_only = true;
+  }
   TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
@@ -1057,6 +1067,8 @@ template <class T>
 void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nvec,
                        unsigned adj_mask) {
   TDLZ_REQUIRE(nvec >= 1 && nvec <= 32, TDLZ_ERR_ARG, "nvec must be in [1, 32]");
+  TDLZ_REQUIRE(sizeof(T) == 4 || !s.mixed_only, TDLZ_ERR_STATE,
+               "q-slot loaded for mixed precision only (TDLZ_MIXED_ONLY=1): no FP64 application");
   ensure_precision<T>(ctx, s);
   alloc_workspace<T>(s, nvec);
   SlotData<T> &d = slot_data<T>(s);
@@ -1071,6 +1083,7 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   const double c = sizeof(cx<T>), re = sizeof(T);
   const double V = (double)br * nvec, G = (double)rows * nr, Gu = (double)s.rows() * nr;
   if (adj_mask) {  // L^H x = J L J x for the flagged vectors
+    if (w.xin.bytes < (size_t)V * sizeof(cx<T>)) w.xin.alloc((size_t)V * sizeof(cx<T>));
     ProfScope ps(pf, st, ST_LANCZOS, 2 * V * c, 0);
     cx<T> *xin = w.xin.template as<cx<T>>();
     for (int v = 0; v < nvec; ++v) {

@@ -10,6 +10,7 @@ Configs (seed 1000 + id unless given):
 * C2  -- hexagonal a=13, c=30 (vacuum slab), 36x36x96, ~5000 PW, 4x4 k grid,
   40 bands, 8 atoms x 8 projectors (2 radial x {s,p}) with full L.sigma.
 * C3  -- hexagonal a=13, c=38, 45x45x144, ~12000 PW, 8x8 k grid, 70 bands.
+* C5  -- the batched form's cell: C3's on a 4x4 k grid, a cutoff per q-point.
 
 The hexagonal atoms sit at the in-plane fractional positions of a CrI3
 monolayer (2 "Cr" + 6 "I" sites) with the layer centred in the cell.
@@ -68,7 +69,19 @@ CONFIGS = {
                  seed=1002, alat=13.0),
     "C3": Config("C3", _hex(13.0, 38.0), (45, 45, 144), 12.7, (8, 8, 1), 70, (0.125, 0, 0), "hex",
                  seed=1003, alat=13.0),
+    # the batched form's cell: C3's cell and grid on a 4x4 k grid; each q-point of the
+    # batch sets its own cutoff (c5_ecut) so that the k+q spheres hold 10000-13000 PW
+    "C5": Config("C5", _hex(13.0, 38.0), (45, 45, 144), 12.7, (4, 4, 1), 70, (0.0625, 0, 0),
+                 "hex", seed=1005, alat=13.0),
 }
+
+
+def c5_ecut(m: int, nq: int = 6) -> float:
+    """Cutoff (Ha) of q-point m = 1..nq of the batched form: plane waves per spinor
+    component from 10000 (m = 1) to 13000 (m = nq) in equal steps, using Np ~ ecut^(3/2)
+    from C3's ~12000 at 12.7 Ha."""
+    npw = 10000.0 + 3000.0 * (m - 1) / max(nq - 1, 1)
+    return 12.7 * (npw / 12000.0) ** (2.0 / 3.0)
 
 # CrI3 monolayer sites, crystal coordinates (in-plane) and layer height offsets
 # relative to the Cr plane in bohr (c = 37.38 bohr in the reference structure).

@@ -130,3 +130,21 @@ def test_non_orthonormal_occupied_states_rejected(torch, ctx):
     with pytest.raises(TdlzError) as e:
         ctx.load_ground_state(dataclasses.replace(gs, coeff_kq=ckq))
     assert e.value.status == TDLZ_ERR_ARG and "orthonormal" in str(e.value)
+
+
+def test_mixed_only_slot_refuses_fp64(torch, ctx, monkeypatch):
+    """A q-slot loaded with TDLZ_MIXED_ONLY=1 (FP64 real-space orbitals released after
+    the FP32 ones are built) applies L in mixed precision as before and refuses FP64
+    (TDLZ_ERR_STATE) instead of reading freed data."""
+    from paper_2203_01120_gb300 import TDLZ_FP64, TdlzError
+    monkeypatch.setenv("TDLZ_MIXED_ONLY", "1")
+    q = ctx.load_ground_state(ground_state("C1"))
+    lv = liouvillian("C1")
+    x = random_br_vector(lv.gs, seed=52)
+    y = apply_mixed(torch, ctx, q, x)
+    ref = lv.apply(x)
+    assert np.linalg.norm(y - ref) <= 2e-5 * np.linalg.norm(ref)
+    xt = torch.as_tensor(x, device="cuda")
+    with pytest.raises(TdlzError) as e:
+        ctx.apply_liouvillian(q, xt, torch.zeros_like(xt), False, TDLZ_FP64)
+    assert e.value.status == 2
