@@ -537,9 +537,18 @@ def run_tdlz(args):
     mus = list(range(args.chains))
     stream = torch.cuda.Stream(device=local)
     ctx = Context(local, stream=stream.cuda_stream)
+    # the CrI3-shaped cells: mixed work on a q-slot holding FP32 data only, FP64 work on a
+    # second context afterwards (both sets of real-space orbitals and workspaces together
+    # would fill most of the device)
+    split = args.config not in ("C1", "C2")
     # ------------------------------------------------------------ e2e (host in/out)
     t0 = time.perf_counter()
-    q = ctx.load_ground_state(gs)
+    if split:
+        os.environ["TDLZ_MIXED_ONLY"] = "1"
+    try:
+        q = ctx.load_ground_state(gs)
+    finally:
+        os.environ.pop("TDLZ_MIXED_ONLY", None)
     t1 = time.perf_counter()
     ch = ctx.chain_create([q] * len(mus), mus, args.steps, args.flavor, TDLZ_MIXED)
     ctx.synchronize()
@@ -581,18 +590,23 @@ def run_tdlz(args):
     fp64_steps = max(3, args.steps // 4)
     m = chi_steps
     chi = None
+    autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     if args.mixed_only:  # profiling runs: the mixed chains above are the whole workload
         sps_fp64, wall_fp64, prof64 = None, None, {}
     else:
-        sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(
-            ctx, q, mus, args.flavor, TDLZ_FP64, 1, fp64_steps, stream, profile=True)
         # ------------------------------------------------ chi error mixed vs FP64
         # C2: the timed chains; larger cells (shape-only occupied states, where the
         # J-metric start vector has a J-norm ~1e-3 of its norm and the PH recursion is
         # ill-conditioned from its first steps) one NH chain over a short prefix
         chi_fl, chi_mus = (args.flavor, mus) if args.config in ("C1", "C2") else ("nh", [0])
-        r64 = ctx.lanczos_run([q] * len(chi_mus), chi_mus, m, chi_fl, TDLZ_FP64)
         r32 = ctx.lanczos_run([q] * len(chi_mus), chi_mus, m, chi_fl, TDLZ_MIXED)
+        if split:
+            ctx.close()
+            ctx = Context(local, stream=stream.cuda_stream)
+            q = ctx.load_ground_state(gs)
+        sps_fp64, wall_fp64, _, prof64, _ = chain_steps_per_s(
+            ctx, q, mus, args.flavor, TDLZ_FP64, 1, fp64_steps, stream, profile=True)
+        r64 = ctx.lanczos_run([q] * len(chi_mus), chi_mus, m, chi_fl, TDLZ_FP64)
         chi = {"steps": m, "flavor": chi_fl, "chains": chi_mus, "omega_mev": [0.0, 100.0, 0.1],
                "eta_mev": 10.0, "tolerance": 1e-4,
                "norm": "per column mu: max over lambda ||chi_mixed - chi_fp64|| / ||chi_fp64[mu][mu]||"}
@@ -616,7 +630,6 @@ def run_tdlz(args):
                 ca = ctx.spectrum(r32, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
                 cb = ctx.spectrum(r32b, 0.0, 100.0, 0.1, 10.0, units=1, itermax0=mm)
                 chi[f"fp32_rounding_spread_{mm}"] = chi_column_errors(cb, ca)
-    autotune = {k: v[0] for k, v in ctx.autotune_report().items()}
     ctx.close()
     # cuFFT on the same batch as one pass: full box, and driven the same pruned way
     cufft = None

@@ -130,6 +130,8 @@ struct QSlot {
   // loaded for mixed precision only (TDLZ_MIXED_ONLY=1): the FP32 data is built at load
   // and the FP64 real-space orbitals are released; FP64 applications are refused
   bool mixed_only = false;
+  size_t dev_total = 0;    // device memory (bytes): sizes the staged pipeline's sub-batches
+  int staged_sub_env = 0;  // TDLZ_STAGED_SUB=n: at most n stacked vectors per staged pass
   bool tensor_gemm = true;  // FP32 V_NL / P_c reductions and updates on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;

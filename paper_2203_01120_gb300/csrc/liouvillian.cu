@@ -600,6 +600,33 @@ __global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restri
 }
 
 
+// Bytes of the staged pipeline's buffers for one stacked vector: the real-space grids,
+// the plane buffer and the stick buffer of every row, complex elements of c bytes.
+double staged_vector_bytes(const QSlot &s, size_t c) {
+  const double per_row = (double)s.nr + (double)s.nplane_max * s.fft[1] * s.fft[2] +
+                         (double)s.nstick_max * s.fft[2];
+  return (double)s.rows() * per_row * (double)c;
+}
+
+// Largest number of stacked vectors in one pass of the staged pipeline: all nvec where
+// their buffers take at most a tenth of the device memory, else the largest count that
+// does (at least one).  Non-decreasing in nvec: the workspace is sized by it.
+int staged_cap(const QSlot &s, size_t c, int nvec) {
+  int n = (int)std::floor(0.1 * (double)s.dev_total / staged_vector_bytes(s, c));
+  n = std::max(1, std::min(n, nvec));
+  if (s.staged_sub_env > 0) n = std::min(n, s.staged_sub_env);
+  return n;
+}
+
+// Vectors per sub-batch of a pass over nvec stacked vectors: the sub-batches balanced
+// under staged_cap (never above it).  Every vector's stages are independent of the
+// others', so the sub-batches change no result.
+int staged_sub(const QSlot &s, size_t c, int nvec) {
+  const int n = staged_cap(s, c, nvec);
+  const int nbatch = (nvec + n - 1) / n;
+  return (nvec + nbatch - 1) / nbatch;
+}
+
 template <class T>
 void alloc_workspace(QSlot &s, int nvec) {
   Workspace<T> &w = slot_ws<T>(s);
@@ -617,14 +644,20 @@ void alloc_workspace(QSlot &s, int nvec) {
       pmax = std::max(pmax, (size_t)planes_density_chunks(s, m, c) * m);
     w.rhopart.alloc(pmax * 4 * (size_t)s.nr * c);
     w.vpot.alloc(nv * s.fft[2] * 6 * (size_t)planes_nnp(s) * c);
+    w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
+    w.rho.alloc(nv * 4 * (size_t)s.nr * c);
+    w.hgrid.alloc(nv * (size_t)s.nr * c);
   } else {
-    w.xr.alloc(nv * s.rows() * s.nr * c);
-    w.i2.alloc(nv * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
-    w.rhopart.alloc((size_t)kDensityGroups * nv * 4 * (size_t)s.nr * c);
-    w.vpot.alloc(nv * 4 * (size_t)s.nr * c);
+    // the real-space stages run over sub-batches of at most ns stacked vectors
+    const size_t ns = (size_t)staged_cap(s, c, nvec);
+    w.xr.alloc(ns * s.rows() * s.nr * c);
+    w.i2.alloc(ns * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+    w.i1.alloc(ns * s.rows() * s.nstick_max * s.fft[2] * c);
+    w.rhopart.alloc((size_t)kDensityGroups * ns * 4 * (size_t)s.nr * c);
+    w.vpot.alloc(ns * 4 * (size_t)s.nr * c);
+    w.rho.alloc(ns * 4 * (size_t)s.nr * c);
+    w.hgrid.alloc(ns * (size_t)s.nr * c);
   }
-  w.rho.alloc(nv * 4 * (size_t)s.nr * c);
-  w.hgrid.alloc(nv * (size_t)s.nr * c);
   w.h.alloc(nv * (size_t)s.br_elems() * c);
   w.xin.reset();  // the adjoint's input copy: allocated on its first use
   size_t batch = nv * 2 * s.nk;
@@ -634,7 +667,6 @@ void alloc_workspace(QSlot &s, int nvec) {
   size_t p1 = (size_t)32 * batch * std::max(s.nproj, 1) * 2 * s.nb;
   size_t p2 = (size_t)32 * batch * s.nb * s.nb;
   w.part.alloc(std::max(p1, p2) * c);
-  w.i1.alloc(nv * s.rows() * s.nstick_max * s.fft[2] * c);
   w.nvec_cap = nvec;
   w.ready = true;
 }
@@ -886,26 +918,28 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   };
   s.plan.init(gs->fft);
   build_stick_tables(s, idx_kq);
-  // Real-space stages: the staged pipeline (real-space grids of every stacked vector in
-  // HBM) where its workspace, planned for six stacked vectors in both precisions, takes
-  // at most 60% of the device; otherwise the fused plane stages, whose workspace is the
-  // stick buffer.  On the 36x36x96 workload the staged pipeline is the faster of the two
-  // (its grid traffic costs less HBM time than the plane stages' extra line transforms
-  // cost issue slots).  TDLZ_PLANES=1 forces the plane stages where the grid allows
-  // them, TDLZ_PLANES=0 the staged pipeline.
+  // Real-space stages, per precision: the staged pipeline (real-space grids of the stacked
+  // vectors in HBM, in sub-batches that take at most a tenth of the device) where one
+  // vector's buffers take at most 30% of the device memory; otherwise the fused plane
+  // stages, whose workspace is the stick buffer.  Where both fit, the staged pipeline is
+  // the faster (its grid traffic costs less HBM time than the plane stages' extra line
+  // transforms cost issue slots).  TDLZ_PLANES=1 forces the plane stages where the grid
+  // allows them, TDLZ_PLANES=0 the staged pipeline.
   {
-    const char *pl_env = std::getenv("TDLZ_PLANES");
-    const double rows = (double)s.rows(), per_row = (double)nr +
-                                                    (double)s.nplane_max * s.fft[1] * s.fft[2] +
-                                                    (double)s.nstick_max * s.fft[2];
-    const double staged_bytes = rows * nr * (16.0 + 8.0) + 6.0 * rows * per_row * (16.0 + 8.0);
     size_t free_b = 0, total_b = 0;
     TDLZ_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    bool want = staged_bytes > 0.6 * (double)total_b;
-    if (pl_env && pl_env[0] == '0') want = false;
-    if (pl_env && pl_env[0] == '1') want = true;
-    s.planes32 = want && planes_supported<float>(s);
-    s.planes64 = want && planes_supported<double>(s);
+    s.dev_total = total_b;
+    const char *sub_env = std::getenv("TDLZ_STAGED_SUB");
+    s.staged_sub_env = sub_env ? std::max(0, std::atoi(sub_env)) : 0;
+    const char *pl_env = std::getenv("TDLZ_PLANES");
+    auto want_planes = [&](size_t c) {
+      bool want = staged_vector_bytes(s, c) > 0.3 * (double)total_b;
+      if (pl_env && pl_env[0] == '0') want = false;
+      if (pl_env && pl_env[0] == '1') want = true;
+      return want;
+    };
+    s.planes32 = want_planes(sizeof(float2)) && planes_supported<float>(s);
+    s.planes64 = want_planes(sizeof(double2)) && planes_supported<double>(s);
   }
   // TDLZ_TC=0 keeps the V_NL / P_c reductions and updates on the CUDA-core GEMMs (A/B timing)
   const char *tc_env = std::getenv("TDLZ_TC");
@@ -1000,11 +1034,12 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
       1.0 / std::sqrt(s.omega), s.rows());
   TDLZ_LAUNCH_CHECK();
   fft3d<double>(s.plan, d.ur.as<double2>(), s.rows(), +1, st);
-  // plane stages read U(r) as z-major slabs; the grid-order copy is kept only while a
-  // staged pipeline (or the FP32 slabs, built lazily) still needs it
+  // plane stages read U(r) as z-major slabs; the FP32 data of either layout are built
+  // later from the slabs, so the grid-order copy goes
   if (s.planes64) {
     planes_build_u<double>(ctx, s, d.ur.as<double2>(), d.us);
-    if (s.planes32) d.ur.reset();
+    TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
+    d.ur.reset();
   }
   // u^lambda = J sigma^lambda U on the k+q sphere (unprojected)
   d.uvec.alloc(3 * brb);
@@ -1040,8 +1075,10 @@ void ensure_precision(Context &ctx, QSlot &s) {
           convert_buf<float>(ctx, d.us, f.us);  // same slab layout
         else
           planes_build_u<float>(ctx, s, d.ur.as<double2>(), f.us);
-      } else {
+      } else if (d.ur.p) {
         convert_buf<float>(ctx, d.ur, f.ur);
+      } else {
+        planes_grid_from_slabs<float>(ctx, s, d.us.as<double2>(), f.ur);
       }
       if (s.nproj > 0) {
         convert_buf<float>(ctx, d.beta, f.beta);
@@ -1102,17 +1139,17 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   cx<T> *h = w.h.template as<cx<T>>();
   const bool use_h = s.kernel_mask & TDLZ_KERNEL_HARTREE, use_xc = s.kernel_mask & TDLZ_KERNEL_XC;
   // Hartree at q (Eq. v_H_q): rho'_0 -> G, 4 pi / |q+G|^2 on the density sphere, -> r
-  auto hartree = [&]() {
-    ProfScope ps(pf, st, ST_HARTREE, 8.0 * nvec * nr * c,
-                 2 * 5.0 * nvec * nr * std::log2((double)nr));
-    long long tot = (long long)nvec * nr;
+  auto hartree = [&](int nv) {
+    ProfScope ps(pf, st, ST_HARTREE, 8.0 * nv * nr * c,
+                 2 * 5.0 * nv * nr * std::log2((double)nr));
+    long long tot = (long long)nv * nr;
     gather_component_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(rho, hg, nr, 4 * nr, tot);
     TDLZ_LAUNCH_CHECK();
-    fft3d<T>(s.plan, hg, nvec, -1, st);
+    fft3d<T>(s.plan, hg, nv, -1, st);
     scale_periodic_kernel<T><<<blocks_for(tot), kThreads, 0, st>>>(
         hg, d.vhfac.template as<T>(), nr, tot);
     TDLZ_LAUNCH_CHECK();
-    fft3d<T>(s.plan, hg, nvec, +1, st);
+    fft3d<T>(s.plan, hg, nv, +1, st);
   };
   const bool planes = sizeof(T) == 4 ? s.planes32 : s.planes64;
   if (planes) {
@@ -1141,7 +1178,7 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
       planes_density<T>(ctx, s, i1, d.us.template as<cx<T>>(), d.wk.template as<T>(),
                         w.rhopart.template as<cx<T>>(), rho, nvec);
     }
-    if (use_h) hartree();
+    if (use_h) hartree(nvec);
     {
       ProfScope ps(pf, st, ST_POTENTIAL,
                    nvec * (5 * nr * c + 14 * nr * re) + pot_bytes, 16.0 * 4 * nr * nvec);
@@ -1164,33 +1201,41 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   } else {
     cx<T> *xr = w.xr.template as<cx<T>>();
     cx<T> *i2 = w.i2.template as<cx<T>>();
-    // 1. sphere -> real space (pruned Z, Y passes; full X pass)
-    pipeline_inverse<T>(ctx, s, x, xr, i1, i2, nvec);  // profiled per stage inside
-    // 2-4. densities and HXC potentials (one set per vector)
-    if (use_h || use_xc) {
-      {
-        ProfScope ps(pf, st, ST_DENSITY, G * c + Gu * c * ((nvec + 2) / 3) + 4 * nvec * nr * c,
-                     (double)nbs * nr * 40.0);
-        launch_density<T>(ctx, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
-                          w.rhopart.template as<cx<T>>(), nk, nb, nr, nvec);
+    const int nsub = staged_sub(s, sizeof(cx<T>), nvec);
+    for (int v0 = 0; v0 < nvec; v0 += nsub) {
+      // vectors v0 .. v0 + m - 1: their grids, plane and stick buffers fill the workspace
+      const int m = std::min(nsub, nvec - v0);
+      const cx<T> *xs = x + (long long)v0 * br;
+      cx<T> *hs = h + (long long)v0 * br;
+      const double Gm = (double)s.rows() * m * nr;
+      // 1. sphere -> real space (pruned Z, Y passes; full X pass)
+      pipeline_inverse<T>(ctx, s, xs, xr, i1, i2, m);  // profiled per stage inside
+      // 2-4. densities and HXC potentials (one set per vector)
+      if (use_h || use_xc) {
+        {
+          ProfScope ps(pf, st, ST_DENSITY, Gm * c + Gu * c * ((m + 2) / 3) + 4 * m * nr * c,
+                       (double)Gm / 2 * 40.0);
+          launch_density<T>(ctx, d.ur.template as<cx<T>>(), xr, d.wk.template as<T>(), rho,
+                            w.rhopart.template as<cx<T>>(), nk, nb, nr, m);
+        }
+        if (use_h) hartree(m);
+        ProfScope ps(pf, st, ST_POTENTIAL, m * (9 * nr * c + 10 * nr * re),
+                     16.0 * 4 * nr * m);
+        for (int v = 0; v < m; ++v) {
+          potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(
+              rho + (long long)v * 4 * nr, hg + (long long)v * nr, d.fxc.template as<T>(),
+              vp + (long long)v * 4 * nr, nr, use_h ? 1 : 0, use_xc ? 1 : 0);
+          TDLZ_LAUNCH_CHECK();
+        }
+      } else {
+        TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
       }
-      if (use_h) hartree();
-      ProfScope ps(pf, st, ST_POTENTIAL, nvec * (9 * nr * c + 10 * nr * re),
-                   16.0 * 4 * nr * nvec);
-      for (int v = 0; v < nvec; ++v) {
-        potential_kernel<T><<<blocks_for(nr), kThreads, 0, st>>>(
-            rho + (long long)v * 4 * nr, hg + (long long)v * nr, d.fxc.template as<T>(),
-            vp + (long long)v * 4 * nr, nr, use_h ? 1 : 0, use_xc ? 1 : 0);
-        TDLZ_LAUNCH_CHECK();
-      }
-    } else {
-      TDLZ_CUDA_TRY(cudaMemsetAsync(vp, 0, w.vpot.bytes, st));
+      // 5-6. local products; pruned X, Y, Z forward passes with the sphere gather and
+      //      + (kin - e) x fused into the last one
+      pipeline_forward<T>(ctx, s, xs, xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(),
+                          d.bfield.template as<T>(), vp, d.kin.template as<T>(),
+                          d.evals.template as<T>(), i1, i2, hs, m);  // profiled inside
     }
-    // 5-6. local products; pruned X, Y, Z forward passes with the sphere gather and
-    //      + (kin - e) x fused into the last one
-    pipeline_forward<T>(ctx, s, x, xr, d.ur.template as<cx<T>>(), d.vloc.template as<T>(),
-                        d.bfield.template as<T>(), vp, d.kin.template as<T>(),
-                        d.evals.template as<T>(), i1, i2, h, nvec);  // profiled inside
   }
   // 7. nonlocal pseudopotential (projector tables shared by all vectors: batch b -> k = b % nk)
   const long long bstride = (long long)nb * 2 * npwx;

@@ -645,6 +645,19 @@ __global__ void u_slab_kernel(const double2 *__restrict__ ur, cx<T> *__restrict_
   }
 }
 
+template <class T>
+__global__ void grid_from_slab_kernel(const double2 *__restrict__ us, cx<T> *__restrict__ ur,
+                                      long long nn, int n3, long long nnp, long long nr,
+                                      long long total) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / nr, r = e - row * nr;
+    const long long i = r / n3, j3 = r - i * n3;
+    const double2 u = us[(row * n3 + j3) * nnp + i];
+    ur[e] = mk<T>((T)u.x, (T)u.y);
+  }
+}
+
 // -------------------------------------------------------------- dispatch
 int threads_of(int n) {
   switch (n) {
@@ -743,6 +756,15 @@ template <class T> void planes_build_u(Context &ctx, QSlot &s, const double2 *ur
 }
 
 template <class T>
+void planes_grid_from_slabs(Context &ctx, QSlot &s, const double2 *us, DevBuf &ur) {
+  const long long nn = (long long)s.fft[0] * s.fft[1], total = s.rows() * s.nr;
+  ur.alloc((size_t)total * sizeof(cx<T>));
+  grid_from_slab_kernel<T><<<blocks_for(total), 256, 0, ctx.stream>>>(
+      us, ur.as<cx<T>>(), nn, s.fft[2], planes_nnp(s), s.nr, total);
+  TDLZ_LAUNCH_CHECK();
+}
+
+template <class T>
 void planes_density(Context &ctx, QSlot &s, const cx<T> *i1t, const cx<T> *us, const T *wk,
                     cx<T> *part, cx<T> *rho, int nvec) {
   const PlTables tb = tables_of(s);
@@ -817,6 +839,8 @@ template bool planes_supported<float>(const QSlot &);
 template bool planes_supported<double>(const QSlot &);
 template void planes_build_u<float>(Context &, QSlot &, const double2 *, DevBuf &);
 template void planes_build_u<double>(Context &, QSlot &, const double2 *, DevBuf &);
+template void planes_grid_from_slabs<float>(Context &, QSlot &, const double2 *, DevBuf &);
+template void planes_grid_from_slabs<double>(Context &, QSlot &, const double2 *, DevBuf &);
 template void planes_density<float>(Context &, QSlot &, const float2 *, const float2 *,
                                     const float *, float2 *, float2 *, int);
 template void planes_density<double>(Context &, QSlot &, const double2 *, const double2 *,

@@ -19,6 +19,11 @@ long long planes_nnp(const QSlot &s);
 // planes_nnp) from the real-space orbitals ur[row][i*n3 + j3].
 template <class T> void planes_build_u(Context &ctx, QSlot &s, const double2 *ur, DevBuf &us);
 
+// The inverse reordering, rounded to T: ur[row][i*n3 + j3] = us[row][j3][i] (the
+// staged pipeline's orbitals from the FP64 slabs, once the grid-order copy is gone).
+template <class T> void planes_grid_from_slabs(Context &ctx, QSlot &s, const double2 *us,
+                                               DevBuf &ur);
+
 // Number of band-side chunks of the density pass for nvec stacked vectors (a
 // function of the problem shape and the device only: it fixes the summation order).
 int planes_density_chunks(const QSlot &s, int nvec, size_t elem);

@@ -46,6 +46,10 @@ class Config:
     lam_so_scale: float = 1.0
     seed: int = 1000
     alat: float = 1.0
+    natom: int = 0              # cubic cells: atoms (0: one for C0*, two otherwise)
+    well_depth: float = 0.0     # Gaussian wells -V exp(-|r - R|^2 / (2 w^2)) added to v_loc,
+    well_width: float = 1.0     # centred at R = first atom + each of well_shifts (bohr)
+    well_shifts: tuple = ((0.0, 0.0, 0.0),)
 
 
 def _cubic(a):
@@ -73,6 +77,14 @@ CONFIGS = {
     # batch sets its own cutoff (c5_ecut) so that the k+q spheres hold 10000-13000 PW
     "C5": Config("C5", _hex(13.0, 38.0), (45, 45, 144), 12.7, (4, 4, 1), 70, (0.0625, 0, 0),
                  "hex", seed=1005, alat=13.0),
+    # a spontaneously magnetic model for the Goldstone check: one electron per cell bound
+    # in a deep Gaussian well (an isolated "atom"), so that the self-consistent Slater
+    # exchange polarises it fully without an external field; the atom's p projectors
+    # (lambda L_z sigma_z / 2) sit off the well's centre so that spin-orbit coupling
+    # reaches the occupied state
+    "CG": Config("CG", _cubic(8.0), (16, 16, 16), 3.8553, (1, 1, 1), 1, (0.02, 0, 0), "cubic",
+                 v_sigma=0.02, b_noncollinear=0.0, seed=1007, alat=8.0, natom=1,
+                 well_depth=3.0, well_width=1.0, well_shifts=((0.9, 0.6, 0.4),)),
 }
 
 
@@ -100,7 +112,7 @@ _CRI3_FRAC = np.array([
 def _atoms(cfg: Config, rng) -> list:
     lat = cfg.lattice
     if cfg.kind == "cubic":
-        natom = 1 if cfg.name.startswith("C0") else 2
+        natom = cfg.natom or (1 if cfg.name.startswith("C0") else 2)
         atoms = []
         for a in range(natom):
             frac = rng.uniform(0.2, 0.8, size=3)
@@ -144,6 +156,22 @@ def _random_real_field(fft, bvec, gcut, sigma, rng):
     f = scipy.fft.ifftn(coef.reshape(fft), workers=-1).ravel() * m.shape[0]
     assert np.max(np.abs(f.imag)) < 1e-9 * max(1.0, np.max(np.abs(f.real)))
     return f.real.copy()
+
+
+def _gaussian_well(fft, lat, bvec, omega, centre, depth, width):
+    """Periodic sum of -depth exp(-|r - R - T|^2 / (2 width^2)) over the lattice vectors T
+    on the grid, from its Fourier series (every G of the grid)."""
+    from .model import grid_miller
+    m = grid_miller(fft)
+    g = m @ bvec
+    g2 = np.sum(g * g, axis=1)
+    vg = -depth * (2 * np.pi * width ** 2) ** 1.5 / omega * np.exp(-0.5 * g2 * width ** 2)
+    vg = vg * np.exp(-1j * (g @ centre))
+    idx = miller_to_index(m, fft)
+    arr = np.zeros(int(np.prod(fft)), dtype=np.complex128)
+    arr[idx] = vg
+    v = scipy.fft.ifftn(arr.reshape(fft)).reshape(-1) * arr.size
+    return np.ascontiguousarray(v.real)
 
 
 def _kpoints(cfg: Config, bvec):
@@ -242,6 +270,9 @@ def make_ground_state(name: str, *, seed: int | None = None, collinear: bool = F
         d[2] = 1.0
     bfield = cfg.b0 * d / np.linalg.norm(d, axis=0)[None, :]
     atoms = _atoms(cfg, rng)
+    for shift in cfg.well_shifts if cfg.well_depth > 0 else ():
+        vloc = vloc + _gaussian_well(fft, lat, bvec, omega, atoms[0].tau + np.asarray(shift),
+                                     cfg.well_depth, cfg.well_width)
     dnl = block_diag([atom_dmatrix(a) for a in atoms])
     nproj = dnl.shape[0] // 2
     kpts = _kpoints(cfg, bvec)

@@ -178,3 +178,27 @@ def test_c3_grid_apply_both_paths(torch, ctx, planes, monkeypatch):
         for k in range(gs.nk):
             assert rel(y64[side, k], ref[side, k]) <= 1e-12, (side, k)
     assert rel(apply_gpu(torch, ctx, q, x, mixed=True), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_staged_sub_batches_change_no_result(torch, monkeypatch, prec):
+    """The staged pipeline runs its real-space stages over sub-batches of the stacked
+    vectors where their grids would take too much memory (one vector at a time on the
+    45x45x144 workload); TDLZ_STAGED_SUB=1 forces one vector per sub-batch on C1, and the
+    grouped NH chains (6 stacked vectors per pass) must equal the unsplit run bit for bit."""
+    from paper_2203_01120_gb300 import Context
+    out = []
+    for sub in (None, "1", "4"):
+        if sub is None:
+            monkeypatch.delenv("TDLZ_STAGED_SUB", raising=False)
+        else:
+            monkeypatch.setenv("TDLZ_STAGED_SUB", sub)
+        c = Context(0)
+        try:
+            q = load(c, ground_state("C1"), monkeypatch, planes=False)
+            out.append(c.lanczos_run([q, q, q], [0, 1, 2], 10, "nh", prec))
+        finally:
+            c.close()
+    for other in out[1:]:
+        for key in ("alpha", "beta", "gamma", "z", "n0", "steps_done", "status"):
+            assert np.array_equal(out[0][key], other[key]), key
