@@ -105,7 +105,12 @@ typedef struct {
 
 /* Lanczos parameters (Sec. 2.5; the paper's itermax, ipol, pseudo_hermitian).
  * Chain c runs on q-slot qslot[c] with start vector v^mu, mu = mu[c] in {0,1,2}
- * (x,y,z), and records z^lambda for all three lambda. */
+ * (the spin components x, y, z: v = (P sigma U, P+ sigma T U)) or 3 (the charge,
+ * sigma^0: v = (P U, -P+ T U)), and records z^lambda for lambda = x, y, z and, with
+ * ncomp = 4, the charge as a fourth (u^0 = (U, T U): the charge density enters the
+ * Y side with +, the magnetisation with -, Eqs. charge_dens_resp_q /
+ * spin_dens_resp_q) -- the 4 x 4 generalised susceptibility of Sec. 2.3.  ncomp 0
+ * means 3. */
 typedef struct {
   int nchain;
   const int *qslot; /* [nchain] */
@@ -113,6 +118,7 @@ typedef struct {
   int nsteps;       /* capacity (itermax) */
   int flavor;       /* tdlz_flavor */
   int precision;    /* tdlz_precision */
+  int ncomp;        /* left vectors: 3 (spin; also 0) or 4 (spin and charge) */
 } tdlz_lanczos_params;
 
 /* Coefficients, caller-owned HOST arrays.  Step j = 0..M-1 stands for the
@@ -122,7 +128,7 @@ typedef struct {
   double *alpha;   /* [nchain][nsteps] complex */
   double *beta;    /* [nchain][nsteps] real    */
   double *gamma;   /* [nchain][nsteps] complex */
-  double *z;       /* [nchain][3][nsteps] complex */
+  double *z;       /* [nchain][ncomp][nsteps] complex */
   double *n0;      /* [nchain] start-vector norm in the flavour's metric */
   double *wk;      /* [nchain] k weight w */
   int *steps_done; /* [nchain] steps whose alpha and z are valid: a chain that breaks
@@ -137,6 +143,7 @@ typedef struct {
   int nchain, nsteps;   /* array strides as in tdlz_lanczos_result */
   const int *steps;     /* [nchain] number of coefficients to use (itermax0) */
   const double *alpha, *beta, *gamma, *z, *n0, *wk;
+  int ncomp;            /* rows of z per chain: 3 (also 0) or 4; chi has as many */
 } tdlz_coeffs;
 
 /* Frequencies start..end step `step` (inclusive), broadening eta; units 0 = Ha,
@@ -206,7 +213,8 @@ tdlz_status tdlz_chain_restore(tdlz_chain *ch, const void *host_image, int64_t b
 /* create + advance(nsteps) + read + destroy. */
 tdlz_status tdlz_lanczos_run(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_lanczos_result *res);
 
-/* chi[nchain][3][nomega] (complex double, caller-owned HOST array) for the
+/* chi[nchain][ncomp][nomega] (complex double, caller-owned HOST array; ncomp = 3
+ * or 4 as in tdlz_coeffs, so row l of chain c is chi_{l, mu_c}) for the
  * frequency grid of sp; FP64 on the GPU, one tridiagonal LU with partial
  * pivoting per (chain, omega).  *nomega receives the grid length; pass
  * chi = NULL to query it. */

@@ -176,10 +176,11 @@ def lanczos_phm(apply_l, v, u_list, nsteps, keep_basis=0):
                         n0, steps, status, 0.0, bq, bp)
 
 
-def run_chain(lv, mu, nsteps, flavor="ph", keep_basis=0):
-    """Chain for column mu of chi: start vector v^mu, left vectors u^x, u^y, u^z."""
+def run_chain(lv, mu, nsteps, flavor="ph", keep_basis=0, ncomp=3):
+    """Chain for column mu of chi: start vector v^mu, left vectors u^x, u^y, u^z (and
+    with ncomp = 4 the charge u^0 as the fourth, for the 4x4 susceptibility)."""
     v = lv.start_vector(mu)
-    u = [lv.left_vector(l) for l in range(3)]
+    u = [lv.left_vector(l) for l in range(ncomp)]
     if flavor == "ph":
         return lanczos_ph(lv.apply, v, u, nsteps, keep_basis)
     if flavor == "phm":

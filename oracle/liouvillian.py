@@ -28,6 +28,14 @@ SIGMA4 = np.concatenate([np.eye(2, dtype=np.complex128)[None], PAULI], axis=0)  
 T_SIGN = np.array([1.0, -1.0, -1.0, -1.0])  # Y-side sign per density component
 
 
+def component(mu):
+    """(sigma, Y-side sign t) of perturbation / observable index mu: 0, 1, 2 = the spin
+    components x, y, z (Eq. spin_dens_resp_q, t = -1) and 3 = the charge (sigma^0,
+    Eq. charge_dens_resp_q, t = +1) of the 4x4 generalised susceptibility."""
+    a = 0 if mu == 3 else mu + 1
+    return SIGMA4[a], T_SIGN[a]
+
+
 def reciprocal(lattice):
     return 2.0 * np.pi * np.linalg.inv(lattice).T
 
@@ -151,21 +159,26 @@ class Liouvillian:
 
     # ------------------------------------------------------------ end vectors
     def sigma_u_on_kq(self, mu):
-        """(2, nk, nocc, 2, npwx): sigma^mu U^side_{n,k} expressed on the k+q sphere."""
+        """(2, nk, nocc, 2, npwx): sigma^mu U^side_{n,k} expressed on the k+q sphere
+        (mu = 3: sigma^0, the charge)."""
         gs = self.gs
+        sig = component(mu)[0]
         out = np.zeros(gs.br_shape, dtype=np.complex128)
         for side in range(2):
             for k in range(gs.nk):
                 box = np.zeros((gs.nocc, 2, self.nr), dtype=np.complex128)
                 box[:, :, self.idx_k[k]] = gs.coeff_k[side, k, :, :, :gs.npw_k[k]]
                 cq = box[:, :, self.idx_kq[k]]
-                out[side, k, :, :, :gs.npw_kq[k]] = np.einsum("st,ntg->nsg", PAULI[mu], cq)
+                out[side, k, :, :, :gs.npw_kq[k]] = np.einsum("st,ntg->nsg", sig, cq)
         return out
 
     def start_vector(self, mu):
-        """v^mu = (P sigma^mu U, P+ sigma^mu T U)  (Sec. 2.5)."""
+        """v^mu = P J u^mu = (P sigma^mu U, -t P+ sigma^mu T U)  (Sec. 2.5; the
+        commutator with the ground state puts J on the perturbation's BR image): for the
+        spin components (P sigma U, P+ sigma T U), for the charge (P U, -P+ T U)."""
         gs = self.gs
         su = self.sigma_u_on_kq(mu)
+        su[1] *= -component(mu)[1]
         for side in range(2):
             for k in range(gs.nk):
                 npw = gs.npw_kq[k]
@@ -173,8 +186,12 @@ class Liouvillian:
         return su
 
     def left_vector(self, lam):
-        """u^lambda = (sigma^lambda U, -sigma^lambda T U)  (Sec. 2.5)."""
-        return jmul(self.sigma_u_on_kq(lam))
+        """u^lambda = (sigma^lambda U, t sigma^lambda T U): the vector whose scalar product
+        with a BR vector is its response density lambda (Eqs. charge_dens_resp_q,
+        spin_dens_resp_q: t = +1 for the charge, -1 for the spin components)."""
+        u = self.sigma_u_on_kq(lam)
+        u[1] *= component(lam)[1]
+        return u
 
 
 def jmul(x):

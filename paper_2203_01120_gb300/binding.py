@@ -43,7 +43,7 @@ class TdlzGroundState(C.Structure):
 
 class TdlzLanczosParams(C.Structure):
     _fields_ = [("nchain", C.c_int), ("qslot", _ip), ("mu", _ip), ("nsteps", C.c_int),
-                ("flavor", C.c_int), ("precision", C.c_int)]
+                ("flavor", C.c_int), ("precision", C.c_int), ("ncomp", C.c_int)]
 
 
 class TdlzLanczosResult(C.Structure):
@@ -53,7 +53,8 @@ class TdlzLanczosResult(C.Structure):
 
 class TdlzCoeffs(C.Structure):
     _fields_ = [("nchain", C.c_int), ("nsteps", C.c_int), ("steps", _ip), ("alpha", _dp),
-                ("beta", _dp), ("gamma", _dp), ("z", _dp), ("n0", _dp), ("wk", _dp)]
+                ("beta", _dp), ("gamma", _dp), ("z", _dp), ("n0", _dp), ("wk", _dp),
+                ("ncomp", C.c_int)]
 
 
 class TdlzSpectrumParams(C.Structure):
@@ -258,11 +259,13 @@ class Context:
                                                     int(precision)))
 
     # -------------------------------------------------------------- Lanczos
-    def chain_create(self, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64):
-        return Chain(self, qslots, mus, nsteps, flavor, precision)
+    def chain_create(self, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64, ncomp=3):
+        """mus: 0, 1, 2 = spin x, y, z perturbations, 3 = the charge; ncomp = 3 records
+        z for the spin components, 4 also for the charge (the 4x4 susceptibility)."""
+        return Chain(self, qslots, mus, nsteps, flavor, precision, ncomp)
 
-    def lanczos_run(self, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64):
-        ch = self.chain_create(qslots, mus, nsteps, flavor, precision)
+    def lanczos_run(self, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64, ncomp=3):
+        ch = self.chain_create(qslots, mus, nsteps, flavor, precision, ncomp)
         try:
             ch.advance(nsteps)
             return ch.read()
@@ -271,8 +274,10 @@ class Context:
 
     def spectrum(self, coeffs, start, end, step, eta, units=1, itermax0=0, itermax=0,
                  extrapolation="no"):
-        """chi[nchain][3][nomega] from a coefficient dict as returned by Chain.read()."""
+        """chi[nchain][ncomp][nomega] from a coefficient dict as returned by Chain.read()
+        (ncomp = the dict's z rows: 3, or 4 with the charge last)."""
         nc, cap = coeffs["beta"].shape
+        nl = int(coeffs["z"].shape[1])
         steps = np.ascontiguousarray(coeffs["steps_done"], dtype=np.int32)
         al = np.ascontiguousarray(coeffs["alpha"], dtype=np.complex128)
         be = np.ascontiguousarray(coeffs["beta"], dtype=np.float64)
@@ -281,12 +286,13 @@ class Context:
         n0 = np.ascontiguousarray(coeffs["n0"], dtype=np.float64)
         wk = np.ascontiguousarray(coeffs["wk"], dtype=np.float64)
         c = TdlzCoeffs(nc, cap, _iptr(steps), _dptr(al.view(np.float64)), _dptr(be),
-                       _dptr(ga.view(np.float64)), _dptr(z.view(np.float64)), _dptr(n0), _dptr(wk))
+                       _dptr(ga.view(np.float64)), _dptr(z.view(np.float64)), _dptr(n0), _dptr(wk),
+                       nl)
         sp = TdlzSpectrumParams(float(start), float(end), float(step), float(eta), int(units),
                                 int(itermax0), int(itermax), EXTRAPOLATION[extrapolation])
         nw = C.c_int()
         self._check(self.lib.tdlz_spectrum(self.h, C.byref(c), C.byref(sp), None, C.byref(nw)))
-        chi = np.zeros((nc, 3, nw.value), dtype=np.complex128)
+        chi = np.zeros((nc, nl, nw.value), dtype=np.complex128)
         self._check(self.lib.tdlz_spectrum(self.h, C.byref(c), C.byref(sp),
                                            _dptr(chi.view(np.float64)), C.byref(nw)))
         return chi
@@ -295,12 +301,13 @@ class Context:
     def spectrum_noalloc(self, dev, start, end, step, eta, units, chi_dev):
         """tdlz_spectrum_noalloc: every array in ``dev`` and ``chi_dev`` is a CUDA tensor
         the caller allocated (steps int32, alpha/gamma/z complex128, beta/n0/wk float64);
-        chi_dev is complex128 [nchain][3][nomega].  Enqueued on the context stream."""
+        chi_dev is complex128 [nchain][ncomp][nomega] (ncomp = z's rows).  Enqueued on the
+        context stream."""
         nc, cap = dev["beta"].shape
         vp = lambda t: C.cast(C.c_void_p(t.data_ptr()), _dp)  # noqa: E731
         c = TdlzCoeffs(nc, cap, C.cast(C.c_void_p(dev["steps_done"].data_ptr()), _ip),
                        vp(dev["alpha"]), vp(dev["beta"]), vp(dev["gamma"]), vp(dev["z"]),
-                       vp(dev["n0"]), vp(dev["wk"]))
+                       vp(dev["n0"]), vp(dev["wk"]), int(dev["z"].shape[1]))
         sp = TdlzSpectrumParams(float(start), float(end), float(step), float(eta), int(units))
         self._check(self.lib.tdlz_spectrum_noalloc(self.h, C.byref(c), C.byref(sp),
                                                    C.c_void_p(chi_dev.data_ptr()),
@@ -333,15 +340,17 @@ class Context:
 class Chain:
     """Lanczos chains advancing on the device (tdlz_chain_*)."""
 
-    def __init__(self, ctx: Context, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64):
+    def __init__(self, ctx: Context, qslots, mus, nsteps, flavor="ph", precision=TDLZ_FP64,
+                 ncomp=3):
         self.ctx = ctx
         self.nchain = len(qslots)
         self.cap = int(nsteps)
+        self.ncomp = int(ncomp)
         self._q = np.ascontiguousarray(qslots, dtype=np.int32)
         self._m = np.ascontiguousarray(mus, dtype=np.int32)
         fl = FLAVORS[flavor] if isinstance(flavor, str) else int(flavor)
         p = TdlzLanczosParams(self.nchain, _iptr(self._q), _iptr(self._m), self.cap, fl,
-                              int(precision))
+                              int(precision), self.ncomp)
         self.h = C.c_void_p()
         ctx._check(ctx.lib.tdlz_chain_create(ctx.h, C.byref(p), C.byref(self.h)))
 
@@ -352,7 +361,8 @@ class Chain:
         nc, m = self.nchain, self.cap
         out = {
             "alpha": np.zeros((nc, m), np.complex128), "beta": np.zeros((nc, m)),
-            "gamma": np.zeros((nc, m), np.complex128), "z": np.zeros((nc, 3, m), np.complex128),
+            "gamma": np.zeros((nc, m), np.complex128),
+            "z": np.zeros((nc, self.ncomp, m), np.complex128),
             "n0": np.zeros(nc), "wk": np.zeros(nc), "steps_done": np.zeros(nc, np.int32),
             "status": np.zeros(nc, np.int32),
         }

@@ -59,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

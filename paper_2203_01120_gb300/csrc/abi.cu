@@ -241,13 +241,16 @@ tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_
   tdlz_status st = guarded(ctx, [&] {
     TDLZ_REQUIRE(p && out, TDLZ_ERR_ARG, "NULL params or output");
     TDLZ_REQUIRE(p->nchain >= 1 && p->nsteps >= 1, TDLZ_ERR_ARG, "nchain and nsteps must be >= 1");
+    TDLZ_REQUIRE(p->ncomp == 0 || p->ncomp == 3 || p->ncomp == 4, TDLZ_ERR_ARG,
+                 "ncomp must be 0 or 3 (spin) or 4 (spin and charge)");
     TDLZ_REQUIRE(p->flavor >= 0 && p->flavor <= 2, TDLZ_ERR_ARG, "unknown flavour");
     TDLZ_REQUIRE(p->precision == TDLZ_FP64 || p->precision == TDLZ_MIXED, TDLZ_ERR_ARG,
                  "unknown precision");
     TDLZ_REQUIRE(p->qslot && p->mu, TDLZ_ERR_ARG, "NULL qslot / mu arrays");
     for (int c = 0; c < p->nchain; ++c) {
       slot_of(ctx, p->qslot[c]);
-      TDLZ_REQUIRE(p->mu[c] >= 0 && p->mu[c] <= 2, TDLZ_ERR_ARG, "mu must be 0, 1 or 2");
+      TDLZ_REQUIRE(p->mu[c] >= 0 && p->mu[c] <= 3, TDLZ_ERR_ARG,
+                   "mu must be 0, 1, 2 (spin x, y, z) or 3 (charge)");
       int same = 0;
       for (int d = 0; d < p->nchain; ++d) same += p->qslot[d] == p->qslot[c];
       TDLZ_REQUIRE(same <= (p->flavor == TDLZ_NONHERMITIAN ? 16 : 32), TDLZ_ERR_ARG,
@@ -259,6 +262,7 @@ tdlz_status tdlz_chain_create(tdlz_ctx *ctx, const tdlz_lanczos_params *p, tdlz_
     ch->set.flavor = p->flavor;
     ch->set.precision = p->precision;
     ch->set.cap = p->nsteps;
+    ch->set.ncomp = p->ncomp == 4 ? 4 : 3;
     // TDLZ_GRAPHS=0 keeps every step eager (A/B timing of the graph replay)
     const char *ge = std::getenv("TDLZ_GRAPHS");
     ch->set.use_graphs = !(ge && ge[0] == '0');
@@ -341,6 +345,8 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
     TDLZ_REQUIRE(c->nchain >= 1 && c->nsteps >= 1, TDLZ_ERR_ARG, "empty coefficient set");
     TDLZ_REQUIRE(c->steps && c->alpha && c->beta && c->gamma && c->z && c->n0 && c->wk,
                  TDLZ_ERR_ARG, "NULL coefficient array");
+    TDLZ_REQUIRE(c->ncomp == 0 || c->ncomp == 3 || c->ncomp == 4, TDLZ_ERR_ARG,
+                 "ncomp must be 0 or 3 (spin) or 4 (spin and charge)");
     TDLZ_REQUIRE(sp->step > 0 && sp->end >= sp->start && std::isfinite(sp->eta) && sp->eta > 0,
                  TDLZ_ERR_ARG, "need step > 0, end >= start and eta > 0");
     TDLZ_REQUIRE(sp->units == 0 || sp->units == 1, TDLZ_ERR_ARG, "units must be 0 (Ha) or 1 (meV)");
@@ -356,7 +362,7 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
       TDLZ_REQUIRE(c->steps[i] >= 0 && c->steps[i] <= c->nsteps, TDLZ_ERR_ARG,
                    "steps out of range");
     const double conv = sp->units == 1 ? 1.0 / 27211.386245988 : 1.0;
-    const int nc = c->nchain, cap = c->nsteps;
+    const int nc = c->nchain, cap = c->nsteps, nl = c->ncomp == 4 ? 4 : 3;
     DevBuf d_steps, d_al, d_be, d_ga, d_z, d_n0, d_wk, d_chi, d_scr;
     cudaStream_t st = ctx->c.stream;
     auto up = [&](DevBuf &b, const void *src, size_t bytes) {
@@ -367,15 +373,16 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
     up(d_al, c->alpha, sizeof(double2) * nc * cap);
     up(d_be, c->beta, sizeof(double) * nc * cap);
     up(d_ga, c->gamma, sizeof(double2) * nc * cap);
-    up(d_z, c->z, sizeof(double2) * nc * 3 * cap);
+    up(d_z, c->z, sizeof(double2) * nc * nl * cap);
     up(d_n0, c->n0, sizeof(double) * nc);
     up(d_wk, c->wk, sizeof(double) * nc);
-    d_chi.alloc(sizeof(double2) * nc * 3 * nw);
+    d_chi.alloc(sizeof(double2) * nc * nl * nw);
     d_scr.alloc(sizeof(double2) * 4 * (size_t)cap * nc * nw);
     SpecArgs a{};
     a.nchain = nc;
     a.nomega = (int)nw;
     a.cap = cap;
+    a.nl = nl;
     a.steps = d_steps.as<int>();
     a.alpha = d_al.as<double2>();
     a.beta = d_be.as<double>();
@@ -395,7 +402,7 @@ tdlz_status tdlz_spectrum(tdlz_ctx *ctx, const tdlz_coeffs *c, const tdlz_spectr
                    TDLZ_ERR_ARG, "itermax0 exceeds the computed steps of a chain");
     a.chi = d_chi.as<double2>();
     launch_spectrum(st, a);
-    TDLZ_CUDA_TRY(cudaMemcpyAsync(chi, d_chi.p, sizeof(double2) * nc * 3 * nw,
+    TDLZ_CUDA_TRY(cudaMemcpyAsync(chi, d_chi.p, sizeof(double2) * nc * nl * nw,
                                   cudaMemcpyDeviceToHost, st));
     TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
   });

@@ -127,6 +127,9 @@ struct QSlot {
   // the Liouvillian of each precision runs the fused plane stages (planes.cu); otherwise
   // the staged pipeline with real-space grids in HBM (pipeline.cu)
   bool planes32 = false, planes64 = false;
+  // the staged pipeline's Y and X line passes of each precision run fused (no plane
+  // buffer in HBM; TDLZ_YX_FUSED=0 keeps the separate passes)
+  bool yx32 = false, yx64 = false;
   // loaded for mixed precision only (TDLZ_MIXED_ONLY=1): the FP32 data is built at load
   // and the FP64 real-space orbitals are released; FP64 applications are refused
   bool mixed_only = false;

@@ -43,14 +43,19 @@ struct Pair {
   int jsign;  // 1: weight -1 on the Y half
 };
 struct Pairs {
-  Pair p[4];
+  Pair p[5];
   int n;
 };
 
+// Partial sums are stored kPStride values per block: alpha's dot and up to four z dots.
+constexpr int kPStride = 5;
 
-// Block-level deterministic sum of nv complex values per thread into out[blockIdx][nv].
+
+// Block-level deterministic sum of NV complex values per thread into
+// out[blockIdx][0..NV) (row stride kPStride).
 template <int NV>
 __device__ void block_sum_store(double2 (&v)[NV], double2 *out) {
+  static_assert(NV <= kPStride, "partial row");
   __shared__ double2 sh[kRedThreads];
   for (int q = 0; q < NV; ++q) {
     sh[threadIdx.x] = v[q];
@@ -62,7 +67,7 @@ __device__ void block_sum_store(double2 (&v)[NV], double2 *out) {
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[(long long)blockIdx.x * NV + q] = sh[0];
+    if (threadIdx.x == 0) out[(long long)blockIdx.x * kPStride + q] = sh[0];
     __syncthreads();
   }
 }
@@ -77,7 +82,9 @@ constexpr int kUnroll = 4;  // independent elements per thread per iteration (lo
 template <class T, int NP>
 __global__ void __launch_bounds__(kRedThreads)
     dots_kernel(Pairs pr, long long n, long long half, double2 *partial) {
-  double2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  double2 acc[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) acc[i] = make_double2(0.0, 0.0);
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
   const cx<T> *A[NP], *B[NP];
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(kRedThreads)
       acc[i].y += (double)ry[i];
     }
   }
-  block_sum_store<4>(acc, partial);
+  block_sum_store<NP>(acc, partial);
 }
 
 // Sum the partials of nv values in fixed order; result into out[nv].
@@ -133,8 +140,8 @@ __device__ void reduce_partials(const double2 *partial, int nblk, int nv, double
   for (int q = 0; q < nv; ++q) {
     double2 s = {0, 0};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-      s.x += partial[(long long)b * 4 + q].x;
-      s.y += partial[(long long)b * 4 + q].y;
+      s.x += partial[(long long)b * kPStride + q].x;
+      s.y += partial[(long long)b * kPStride + q].y;
     }
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -153,11 +160,11 @@ __device__ void reduce_partials(const double2 *partial, int nblk, int nv, double
 __device__ __forceinline__ bool finite2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
 
 // ---------------------------------------------------------------- scalars
-// Stage A: alpha and z from the dots (d0 = alpha source, d1..3 = q^H u^l).
+// Stage A: alpha and z from the dots (d0 = alpha source, d1..nz = q^H u^l).
 __global__ void scalar_a_kernel(const double2 *partial, int nblk, ChainScalars *cs,
-                                ChainCoeffs cf, int flavor) {
-  __shared__ double2 d[4];
-  reduce_partials(partial, nblk, 4, d);
+                                ChainCoeffs cf, int flavor, int nz) {
+  __shared__ double2 d[kPStride];
+  reduce_partials(partial, nblk, 1 + nz, d);
   if (threadIdx.x != 0) return;
   if (cs->stopped) return;
   int j = cs->step;
@@ -170,8 +177,12 @@ __global__ void scalar_a_kernel(const double2 *partial, int nblk, ChainScalars *
     alpha = make_double2(d[0].x, 0.0);
   cs->alpha = alpha;
   cf.alpha[j] = alpha;
-  for (int l = 0; l < 3; ++l) cf.z[(long long)l * cf.cap + j] = d[1 + l];
-  if (!finite2(alpha) || !finite2(d[1]) || !finite2(d[2]) || !finite2(d[3])) {
+  bool finite = finite2(alpha);
+  for (int l = 0; l < nz; ++l) {
+    cf.z[(long long)l * cf.cap + j] = d[1 + l];
+    finite = finite && finite2(d[1 + l]);
+  }
+  if (!finite) {
     cs->status = TDLZ_ERR_NUMERIC;
     cs->stopped = 1;
     cs->steps_done = j;  // step j has no valid alpha or z: the chain ends before it
@@ -181,7 +192,7 @@ __global__ void scalar_a_kernel(const double2 *partial, int nblk, ChainScalars *
 // Stage B: beta, gamma, signs and rescale factors from c (d0) and norms (d1, d2).
 __global__ void scalar_b_kernel(const double2 *partial, int nblk, ChainScalars *cs,
                                 ChainCoeffs cf, int flavor) {
-  __shared__ double2 d[4];
+  __shared__ double2 d[kPStride];
   reduce_partials(partial, nblk, 3, d);
   if (threadIdx.x != 0) return;
   if (cs->stopped) {
@@ -253,7 +264,7 @@ __global__ void scalar_b_kernel(const double2 *partial, int nblk, ChainScalars *
 // Initial normalisation: c0 = d0 (J-norm, norm or M-norm of v).
 __global__ void scalar_init_kernel(const double2 *partial, int nblk, ChainScalars *cs,
                                    int flavor) {
-  __shared__ double2 d[4];
+  __shared__ double2 d[kPStride];
   reduce_partials(partial, nblk, 1, d);
   if (threadIdx.x != 0) return;
   double c0 = d[0].x;
@@ -371,42 +382,43 @@ __global__ void __launch_bounds__(kRedThreads)
   block_sum_store<4>(acc, partial);
 }
 
-// NH, the M <= 4 chains of one group at once: partial[c][blk][0..3] = (p~_c^H J a_c,
-// q_c^H u^0, q_c^H u^1, q_c^H u^2), each u^l read once for every chain of the group.
+// NH, the M <= 4 chains of one group at once: partial[c][blk][0..NZ] = (p~_c^H J a_c,
+// q_c^H u^0, .., q_c^H u^(NZ-1)), each u^l read once for every chain of the group.
 struct NhGroupDots {
   const void *p[4], *a[4], *q[4];
-  const void *u[3];
+  const void *u[4];
 };
 constexpr int kGroupUnroll = 2;
-template <class T, int M>
+template <class T, int M, int NZ>
 __global__ void __launch_bounds__(kRedThreads)
     nh_group_dots_kernel(NhGroupDots g, long long n, long long half, double2 *partial) {
-  double2 acc[M][4];
+  constexpr int NA = NZ + 1;
+  double2 acc[M][NA];
 #pragma unroll
   for (int c = 0; c < M; ++c)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[c][i] = make_double2(0.0, 0.0);
+    for (int i = 0; i < NA; ++i) acc[c][i] = make_double2(0.0, 0.0);
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const long long b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
   const long long bd = blockDim.x;
-  const cx<T> *U[3] = {reinterpret_cast<const cx<T> *>(g.u[0]),
-                       reinterpret_cast<const cx<T> *>(g.u[1]),
-                       reinterpret_cast<const cx<T> *>(g.u[2])};
+  const cx<T> *U[NZ];
+#pragma unroll
+  for (int l = 0; l < NZ; ++l) U[l] = reinterpret_cast<const cx<T> *>(g.u[l]);
   long long e = b0 + threadIdx.x;
   while (e < b1) {
-    T rx[M][4], ry[M][4];
+    T rx[M][NA], ry[M][NA];
 #pragma unroll
     for (int c = 0; c < M; ++c)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) rx[c][i] = ry[c][i] = T(0);
+      for (int i = 0; i < NA; ++i) rx[c][i] = ry[c][i] = T(0);
     for (int it = 0; it < kRun / kGroupUnroll && e < b1; ++it) {
-      cx<T> uv[kGroupUnroll][3], pv[kGroupUnroll][M], av[kGroupUnroll][M], qv[kGroupUnroll][M];
+      cx<T> uv[kGroupUnroll][NZ], pv[kGroupUnroll][M], av[kGroupUnroll][M], qv[kGroupUnroll][M];
 #pragma unroll
       for (int w = 0; w < kGroupUnroll; ++w) {
         const long long ew = e + w * bd;
         const bool in = ew < b1;
 #pragma unroll
-        for (int l = 0; l < 3; ++l) uv[w][l] = in ? U[l][ew] : czero<T>();
+        for (int l = 0; l < NZ; ++l) uv[w][l] = in ? U[l][ew] : czero<T>();
 #pragma unroll
         for (int c = 0; c < M; ++c) {
           pv[w][c] = in ? reinterpret_cast<const cx<T> *>(g.p[c])[ew] : czero<T>();
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(kRedThreads)
           rx[c][0] += sg * (pv[w][c].x * av[w][c].x + pv[w][c].y * av[w][c].y);
           ry[c][0] += sg * (pv[w][c].x * av[w][c].y - pv[w][c].y * av[w][c].x);
 #pragma unroll
-          for (int l = 0; l < 3; ++l) {
+          for (int l = 0; l < NZ; ++l) {
             rx[c][1 + l] += qv[w][c].x * uv[w][l].x + qv[w][c].y * uv[w][l].y;
             ry[c][1 + l] += qv[w][c].x * uv[w][l].y - qv[w][c].y * uv[w][l].x;
           }
@@ -433,13 +445,14 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int c = 0; c < M; ++c)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < NA; ++i) {
         acc[c][i].x += (double)rx[c][i];
         acc[c][i].y += (double)ry[c][i];
       }
   }
 #pragma unroll
-  for (int c = 0; c < M; ++c) block_sum_store<4>(acc[c], partial + (long long)c * gridDim.x * 4);
+  for (int c = 0; c < M; ++c)
+    block_sum_store<NA>(acc[c], partial + (long long)c * gridDim.x * kPStride);
 }
 
 // x_v *= *s_v for the nv vectors of a set (the new Lanczos vectors of a group)
@@ -475,7 +488,8 @@ void launch_dots(Context &ctx, Pairs pr, long long n, long long half, double2 *p
     case 1: dots_kernel<T, 1><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
     case 2: dots_kernel<T, 2><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
     case 3: dots_kernel<T, 3><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
-    default: dots_kernel<T, 4><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+    case 4: dots_kernel<T, 4><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
+    default: dots_kernel<T, 5><<<kRedBlocks, kRedThreads, 0, ctx.stream>>>(pr, n, half, partial); break;
   }
   TDLZ_LAUNCH_CHECK();
 }
@@ -501,7 +515,7 @@ template void jflip_copy<float>(Context &, QSlot &, const float2 *, float2 *);
 template <class T>
 void ChainSet::init_impl() {
   const size_t c = sizeof(cx<T>);
-  red.alloc((size_t)kRedBlocks * 4 * 16 * sizeof(double2));  // up to 16 chains per group
+  red.alloc((size_t)kRedBlocks * kPStride * 16 * sizeof(double2));  // up to 16 chains per group
   for (size_t i = 0; i < chains.size(); ++i) {
     Chain &ch = chains[i];
     int g = -1;
@@ -528,13 +542,13 @@ void ChainSet::init_impl() {
     for (int k = 0; k < nslot; ++k) gr.slot[k] = (char *)gr.vec.p + (size_t)k * gr.nv * n * c;
     for (int mi = 0; mi < m; ++mi) {
       Chain &ch = chains[gr.members[mi]];
-      ch.coef.alloc((size_t)cap * (sizeof(double2) * 5 + sizeof(double)));
+      ch.coef.alloc((size_t)cap * (sizeof(double2) * 6 + sizeof(double)));
       TDLZ_CUDA_TRY(cudaMemsetAsync(ch.coef.p, 0, ch.coef.bytes, ctx->stream));
       ch.cf.cap = cap;
       ch.cf.alpha = ch.coef.as<double2>();
       ch.cf.gamma = ch.cf.alpha + cap;
       ch.cf.z = ch.cf.gamma + cap;
-      ch.cf.beta = reinterpret_cast<double *>(ch.cf.z + 3 * (size_t)cap);
+      ch.cf.beta = reinterpret_cast<double *>(ch.cf.z + 4 * (size_t)cap);
       ch.sc.alloc(sizeof(ChainScalars));
       TDLZ_CUDA_TRY(cudaMemsetAsync(ch.sc.p, 0, ch.sc.bytes, ctx->stream));
       start_vector<T>(*ctx, s, ch.mu, (cx<T> *)gr.slot[0] + mi * n);
@@ -594,19 +608,25 @@ void ChainSet::advance_impl(int nsteps) {
             gd.p[mi] = S0 + (m + mi) * n;
             gd.a[mi] = S2 + mi * n;
           }
-          for (int l = 0; l < 3; ++l) gd.u[l] = u + l * n;
+          for (int l = 0; l < ncomp; ++l) gd.u[l] = u + l * n;
+#define TDLZ_NH_DOTS(MM)                                                                   \
+  if (ncomp == 4)                                                                           \
+    nh_group_dots_kernel<T, MM, 4><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); \
+  else                                                                                      \
+    nh_group_dots_kernel<T, MM, 3><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part);
           switch (m) {
-            case 1: nh_group_dots_kernel<T, 1><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
-            case 2: nh_group_dots_kernel<T, 2><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
-            case 3: nh_group_dots_kernel<T, 3><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
-            default: nh_group_dots_kernel<T, 4><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(gd, n, half, part); break;
+            case 1: TDLZ_NH_DOTS(1) break;
+            case 2: TDLZ_NH_DOTS(2) break;
+            case 3: TDLZ_NH_DOTS(3) break;
+            default: TDLZ_NH_DOTS(4) break;
           }
+#undef TDLZ_NH_DOTS
           TDLZ_LAUNCH_CHECK();
-          const long long pstride = (long long)kRedBlocks * 4;
+          const long long pstride = (long long)kRedBlocks * kPStride;
           for (int mi = 0; mi < m; ++mi) {
             Chain &ch = chains[gr.members[mi]];
             scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(
-                part + mi * pstride, kRedBlocks, ch.sc.as<ChainScalars>(), ch.cf, flavor);
+                part + mi * pstride, kRedBlocks, ch.sc.as<ChainScalars>(), ch.cf, flavor, ncomp);
             TDLZ_LAUNCH_CHECK();
           }
           ScaleSet ss{};
@@ -640,11 +660,12 @@ void ChainSet::advance_impl(int nsteps) {
           cx<T> *Q = S0 + mi * n, *P = S0 + (m + mi) * n, *QP = S1 + mi * n,
                 *PP = S1 + (m + mi) * n, *A = S2 + mi * n, *B = S2 + (m + mi) * n;
           Pairs pr{};
-          pr.n = 4;
+          pr.n = 1 + ncomp;
           pr.p[0] = Pair{P, A, 1};  // p^H a = p~^H J a
-          for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
+          for (int l = 0; l < ncomp; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
           launch_dots<T>(*ctx, pr, n, half, part);
-          scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor,
+                                                              ncomp);
           TDLZ_LAUNCH_CHECK();
           update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(A, Q, QP, B, P, PP, cs,
                                                                        flavor, n, half, part);
@@ -665,11 +686,12 @@ void ChainSet::advance_impl(int nsteps) {
           ChainScalars *cs = ch.sc.as<ChainScalars>();
           cx<T> *Q = S0 + mi * n, *QP = S1 + mi * n, *A = S2 + mi * n;
           Pairs pr{};
-          pr.n = 4;
+          pr.n = 1 + ncomp;
           pr.p[0] = Pair{Q, A, 1};
-          for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
+          for (int l = 0; l < ncomp; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
           launch_dots<T>(*ctx, pr, n, half, part);
-          scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor);
+          scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf, flavor,
+                                                              ncomp);
           TDLZ_LAUNCH_CHECK();
           update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
               A, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
@@ -690,12 +712,12 @@ void ChainSet::advance_impl(int nsteps) {
             ChainScalars *cs = ch.sc.as<ChainScalars>();
             cx<T> *Q = S0 + mi * n, *QP = S1 + mi * n, *LQ = S2 + mi * n;
             Pairs pr{};
-            pr.n = 4;
+            pr.n = 1 + ncomp;
             pr.p[0] = Pair{LQ, LQ, 1};
-            for (int l = 0; l < 3; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
+            for (int l = 0; l < ncomp; ++l) pr.p[1 + l] = Pair{Q, u + l * n, 0};
             launch_dots<T>(*ctx, pr, n, half, part);
             scalar_a_kernel<<<1, kRedThreads, 0, ctx->stream>>>(part, kRedBlocks, cs, ch.cf,
-                                                                flavor);
+                                                                flavor, ncomp);
             TDLZ_LAUNCH_CHECK();
             update_kernel<T><<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(
                 LQ, Q, QP, nullptr, nullptr, nullptr, cs, flavor, n, half, part);
@@ -796,6 +818,7 @@ void ChainSet::capture_two_steps() {
 // eager step (which also sizes every workspace), then pairs of steps replayed
 // from the captured graph, then the remainder eagerly.
 void ChainSet::advance(int nsteps) {
+  NvtxRange range("tdlz/advance");
   if (!use_graphs || ctx->prof.on || nsteps < 4) {
     advance_eager(nsteps);
     return;
@@ -806,7 +829,11 @@ void ChainSet::advance(int nsteps) {
   for (const Group &g : groups) room = std::min(room, cap - g.host_step);
   const int pairs = room / 2;
   if (pairs > 0) {
-    if (!gexec || graph_key != slot_key()) capture_two_steps();
+    if (!gexec || graph_key != slot_key()) {
+      NvtxRange cap_range("tdlz/capture");
+      capture_two_steps();
+    }
+    NvtxRange replay_range("tdlz/graph_replay");
     for (int p = 0; p < pairs; ++p) {
       TDLZ_CUDA_TRY(cudaGraphLaunch(gexec, ctx->stream));
       g_launches.fetch_add(graph_kernels);
@@ -824,9 +851,9 @@ void ChainSet::read(tdlz_lanczos_result *res) {
     Chain &ch = chains[c];
     ChainScalars hs;
     TDLZ_CUDA_TRY(cudaMemcpy(&hs, ch.sc.p, sizeof(hs), cudaMemcpyDeviceToHost));
-    std::vector<double2> buf((size_t)cap * 5);
+    std::vector<double2> buf((size_t)cap * 6);
     std::vector<double> bet(cap);
-    TDLZ_CUDA_TRY(cudaMemcpy(buf.data(), ch.cf.alpha, sizeof(double2) * 5 * cap,
+    TDLZ_CUDA_TRY(cudaMemcpy(buf.data(), ch.cf.alpha, sizeof(double2) * 6 * cap,
                              cudaMemcpyDeviceToHost));
     TDLZ_CUDA_TRY(cudaMemcpy(bet.data(), ch.cf.beta, sizeof(double) * cap, cudaMemcpyDeviceToHost));
     int done = hs.steps_done;
@@ -843,10 +870,10 @@ void ChainSet::read(tdlz_lanczos_result *res) {
         res->gamma[2 * ((size_t)c * cap + j) + 1] = v.y;
       }
     if (res->z)
-      for (int l = 0; l < 3; ++l)
+      for (int l = 0; l < ncomp; ++l)
         for (int j = 0; j < cap; ++j) {
           double2 v = j < done ? buf[2 * (size_t)cap + (size_t)l * cap + j] : make_double2(0, 0);
-          size_t o = 2 * (((size_t)c * 3 + l) * cap + j);
+          size_t o = 2 * (((size_t)c * ncomp + l) * cap + j);
           res->z[o] = v.x;
           res->z[o + 1] = v.y;
         }
@@ -867,8 +894,9 @@ void ChainSet::read(tdlz_lanczos_result *res) {
 namespace {
 struct RestartHeader {
   char magic[8];
-  int version, flavor, precision, nchain, ngroup, cap;
+  int version, flavor, precision, nchain, ngroup, cap, ncomp;
 };
+constexpr int kRestartVersion = 2;
 size_t vec_elem_bytes(int precision) { return precision == TDLZ_FP64 ? 16 : 8; }
 int nslots(int flavor) { return flavor == TDLZ_PSEUDOHERMITIAN_POSDEF ? 4 : 3; }
 }  // namespace
@@ -879,7 +907,7 @@ size_t ChainSet::state_bytes() const {
     const QSlot &s = *ctx->slots[g.qslot];
     b += (size_t)nslots(flavor) * g.nv * s.br_elems() * vec_elem_bytes(precision);
   }
-  b += chains.size() * (sizeof(ChainScalars) + (size_t)cap * (5 * sizeof(double2) + sizeof(double)));
+  b += chains.size() * (sizeof(ChainScalars) + (size_t)cap * (6 * sizeof(double2) + sizeof(double)));
   return b;
 }
 
@@ -889,12 +917,13 @@ void ChainSet::save(void *host, size_t bytes) {
   char *p = static_cast<char *>(host);
   RestartHeader h{};
   std::memcpy(h.magic, "TDLZRST", 8);
-  h.version = 1;
+  h.version = kRestartVersion;
   h.flavor = flavor;
   h.precision = precision;
   h.nchain = (int)chains.size();
   h.ngroup = (int)groups.size();
   h.cap = cap;
+  h.ncomp = ncomp;
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
   for (const Chain &c : chains) {
@@ -914,7 +943,7 @@ void ChainSet::save(void *host, size_t bytes) {
       p += sb;
     }
   }
-  const size_t cb = (size_t)cap * (5 * sizeof(double2) + sizeof(double));
+  const size_t cb = (size_t)cap * (6 * sizeof(double2) + sizeof(double));
   for (const Chain &c : chains) {
     TDLZ_CUDA_TRY(cudaMemcpy(p, c.sc.p, sizeof(ChainScalars), cudaMemcpyDeviceToHost));
     p += sizeof(ChainScalars);
@@ -929,10 +958,10 @@ void ChainSet::restore(const void *host, size_t bytes) {
   RestartHeader h;
   std::memcpy(&h, p, sizeof(h));
   p += sizeof(h);
-  TDLZ_REQUIRE(std::memcmp(h.magic, "TDLZRST", 8) == 0 && h.version == 1, TDLZ_ERR_ARG,
-               "not a tdlz restart image");
+  TDLZ_REQUIRE(std::memcmp(h.magic, "TDLZRST", 8) == 0 && h.version == kRestartVersion,
+               TDLZ_ERR_ARG, "not a tdlz restart image");
   TDLZ_REQUIRE(h.flavor == flavor && h.precision == precision && h.nchain == (int)chains.size() &&
-                   h.ngroup == (int)groups.size(),
+                   h.ngroup == (int)groups.size() && h.ncomp == ncomp,
                TDLZ_ERR_ARG, "restart image was saved from a different chain set");
   TDLZ_REQUIRE(h.cap <= cap, TDLZ_ERR_ARG, "restart image holds more steps than this capacity");
   for (const Chain &c : chains) {
@@ -946,7 +975,7 @@ void ChainSet::restore(const void *host, size_t bytes) {
   for (const Group &g : groups)
     need += (size_t)nslots(flavor) * g.nv * ctx->slots[g.qslot]->br_elems() *
             vec_elem_bytes(precision);
-  const size_t cb_old = (size_t)h.cap * (5 * sizeof(double2) + sizeof(double));
+  const size_t cb_old = (size_t)h.cap * (6 * sizeof(double2) + sizeof(double));
   need += chains.size() * (sizeof(ChainScalars) + cb_old);
   TDLZ_REQUIRE(bytes >= need, TDLZ_ERR_ARG, "restart image truncated");
   std::vector<int> steps(groups.size());
@@ -967,15 +996,15 @@ void ChainSet::restore(const void *host, size_t bytes) {
   for (Chain &c : chains) {
     TDLZ_CUDA_TRY(cudaMemcpy(c.sc.p, p, sizeof(ChainScalars), cudaMemcpyHostToDevice));
     p += sizeof(ChainScalars);
-    // coefficient block [alpha cap][gamma cap][z 3 cap][beta cap]: copy each part
+    // coefficient block [alpha cap][gamma cap][z 4 cap][beta cap]: copy each part
     const double2 *src = reinterpret_cast<const double2 *>(p);
     TDLZ_CUDA_TRY(cudaMemcpy(c.cf.alpha, src, h.cap * sizeof(double2), cudaMemcpyHostToDevice));
     TDLZ_CUDA_TRY(cudaMemcpy(c.cf.gamma, src + h.cap, h.cap * sizeof(double2),
                              cudaMemcpyHostToDevice));
-    for (int l = 0; l < 3; ++l)
+    for (int l = 0; l < 4; ++l)
       TDLZ_CUDA_TRY(cudaMemcpy(c.cf.z + (size_t)l * cap, src + (size_t)(2 + l) * h.cap,
                                h.cap * sizeof(double2), cudaMemcpyHostToDevice));
-    TDLZ_CUDA_TRY(cudaMemcpy(c.cf.beta, reinterpret_cast<const double *>(src + 5 * (size_t)h.cap),
+    TDLZ_CUDA_TRY(cudaMemcpy(c.cf.beta, reinterpret_cast<const double *>(src + 6 * (size_t)h.cap),
                              h.cap * sizeof(double), cudaMemcpyHostToDevice));
     p += cb_old;
   }

@@ -19,12 +19,12 @@ struct ChainCoeffs {
   int cap;
   double2 *alpha;  // [cap]
   double2 *gamma;  // [cap]
-  double2 *z;      // [3][cap]
+  double2 *z;      // [4][cap] (z^x, z^y, z^z, and the charge's where ncomp = 4)
   double *beta;    // [cap]
 };
 
 struct Chain {
-  int qslot = 0, mu = 0;
+  int qslot = 0, mu = 0;  // mu = 0, 1, 2: sigma^x,y,z perturbation; 3: the charge
   int group = -1, index = 0;  // its group and position in the group's vector blocks
   DevBuf coef, sc;
   ChainCoeffs cf{};
@@ -43,6 +43,7 @@ struct Group {
 struct ChainSet {
   Context *ctx = nullptr;
   int flavor = 0, precision = 0, cap = 0;
+  int ncomp = 3;  // left vectors u^l recorded per step: 3 (spin) or 4 (spin and charge)
   std::vector<Chain> chains;
   std::vector<Group> groups;
   DevBuf red;

@@ -565,7 +565,10 @@ __global__ void fxc_kernel(const double *__restrict__ n0, const double *__restri
 
 // ---------------------------------------------------------- start vectors
 // v[b][n][s][g] = sum_t sigma^mu[s][t] c_k[b][n][t][map[g]]  (G of the k+q sphere
-// found in the k sphere; 0 otherwise).  ysign multiplies the Y side.
+// found in the k sphere; 0 otherwise), mu = 0, 1, 2: the Pauli matrices, 3: sigma^0
+// (the charge).  ysign multiplies the Y side of the spin components; the charge
+// density has the opposite Y-side sign (Eqs. charge_dens_resp_q, spin_dens_resp_q),
+// so the charge's Y side is multiplied by -ysign.
 template <class T>
 __global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restrict__ map, int mu,
                                cx<T> *__restrict__ out, int nk, int nb, int npwx, T ysign) {
@@ -589,11 +592,14 @@ __global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restri
     } else if (mu == 1) {  // sigma_y: (-i c1, i c0)
       o0 = mk<T>(c1.y, -c1.x);
       o1 = mk<T>(-c0.y, c0.x);
-    } else {  // sigma_z
+    } else if (mu == 2) {  // sigma_z
       o0 = c0;
       o1 = mk<T>(-c1.x, -c1.y);
+    } else {  // sigma^0
+      o0 = c0;
+      o1 = c1;
     }
-    T sg = side == 1 ? ysign : T(1);
+    T sg = side == 1 ? (mu == 3 ? -ysign : ysign) : T(1);
     out[(band * 2) * npwx + g] = cscale<T>(o0, sg);
     out[(band * 2 + 1) * npwx + g] = cscale<T>(o1, sg);
   }
@@ -603,7 +609,9 @@ __global__ void sigma_u_kernel(const cx<T> *__restrict__ ck, const int *__restri
 // Bytes of the staged pipeline's buffers for one stacked vector: the real-space grids,
 // the plane buffer and the stick buffer of every row, complex elements of c bytes.
 double staged_vector_bytes(const QSlot &s, size_t c) {
-  const double per_row = (double)s.nr + (double)s.nplane_max * s.fft[1] * s.fft[2] +
+  const bool fused = c == sizeof(float2) ? s.yx32 : s.yx64;
+  const double per_row = (double)s.nr +
+                         (fused ? 0.0 : (double)s.nplane_max * s.fft[1] * s.fft[2]) +
                          (double)s.nstick_max * s.fft[2];
   return (double)s.rows() * per_row * (double)c;
 }
@@ -650,8 +658,12 @@ void alloc_workspace(QSlot &s, int nvec) {
   } else {
     // the real-space stages run over sub-batches of at most ns stacked vectors
     const size_t ns = (size_t)staged_cap(s, c, nvec);
+    const bool fused = sizeof(T) == 4 ? s.yx32 : s.yx64;
     w.xr.alloc(ns * s.rows() * s.nr * c);
-    w.i2.alloc(ns * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
+    if (fused)
+      w.i2.reset();  // the fused Y + X passes keep the planes on chip
+    else
+      w.i2.alloc(ns * s.rows() * s.nplane_max * s.fft[1] * s.fft[2] * c);
     w.i1.alloc(ns * s.rows() * s.nstick_max * s.fft[2] * c);
     w.rhopart.alloc((size_t)kDensityGroups * ns * 4 * (size_t)s.nr * c);
     w.vpot.alloc(ns * 4 * (size_t)s.nr * c);
@@ -712,6 +724,7 @@ void host_parallel_for(long long n, F &&f) {
 }
 
 void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
+  NvtxRange range("tdlz/load_ground_state");
   // ---- validation (host; nothing launched on failure)
   TDLZ_REQUIRE(gs != nullptr, TDLZ_ERR_ARG, "ground state is NULL");
   TDLZ_REQUIRE(gs->nk >= 1 && gs->nocc >= 1 && gs->npwx >= 1 && gs->nproj >= 0, TDLZ_ERR_ARG,
@@ -931,6 +944,10 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     s.dev_total = total_b;
     const char *sub_env = std::getenv("TDLZ_STAGED_SUB");
     s.staged_sub_env = sub_env ? std::max(0, std::atoi(sub_env)) : 0;
+    const char *yx_env = std::getenv("TDLZ_YX_FUSED");
+    const bool yx_on = yx_env && yx_env[0] == '1';
+    s.yx32 = yx_on && yx_fused_supported<float>(s);
+    s.yx64 = yx_on && yx_fused_supported<double>(s);
     const char *pl_env = std::getenv("TDLZ_PLANES");
     auto want_planes = [&](size_t c) {
       bool want = staged_vector_bytes(s, c) > 0.3 * (double)total_b;
@@ -1041,9 +1058,10 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
     d.ur.reset();
   }
-  // u^lambda = J sigma^lambda U on the k+q sphere (unprojected)
-  d.uvec.alloc(3 * brb);
-  for (int l = 0; l < 3; ++l) {
+  // u^lambda = (sigma^lambda U, t sigma^lambda T U) on the k+q sphere (unprojected):
+  // t = -1 for the spin components x, y, z, +1 for the charge (lambda = 3)
+  d.uvec.alloc(4 * brb);
+  for (int l = 0; l < 4; ++l) {
     sigma_u_kernel<double><<<blocks_for(2LL * nk * nb * npwx), kThreads, 0, st>>>(
         s.coeff_k.as<double2>(), s.map_kq_k.as<int>(), l, d.uvec.as<double2>() + l * s.br_elems(),
         nk, nb, npwx, -1.0);

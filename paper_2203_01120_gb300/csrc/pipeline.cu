@@ -789,6 +789,128 @@ __global__ void __launch_bounds__(kRegMaxThreads)
   }
 }
 
+// ------------------------------------------- fused Y + X line passes
+// One CTA per (row, chunk of kJ3 consecutive z planes) of a square x-y grid: the Y
+// lines of the sphere's planes, then the X lines of the whole box, the planes held in
+// shared memory between the two, so the plane buffer never reaches HBM.  Every line is
+// transformed in one thread's registers by the same plan and in the same order as in
+// the separate passes above, so the results are identical to theirs.
+// Shared memory yb[p][j2][jj] (p < nplane, j2 < N, jj < kJ3): the plane stride is an
+// odd multiple of 8 elements, so the two half-warp phases of a warp's 8-byte accesses
+// (lanes (p, jj), p = 0..3) fall on disjoint banks.
+constexpr int kJ3 = 8;
+template <int N> __host__ __device__ constexpr int yx_pstride() {
+  return (N * kJ3) % 16 == 8 ? N * kJ3 : N * kJ3 + 8;
+}
+template <int N> constexpr int yx_threads() { return 32 * ((N * kJ3 + 63) / 64); }
+constexpr int kYXMaxThreads = 192;
+
+template <class T, int N>
+__global__ void __launch_bounds__(kYXMaxThreads)
+    inv_yx_reg_kernel(const cx<T> *__restrict__ i1, cx<T> *__restrict__ xr,
+                      const int *__restrict__ npl, const int *__restrict__ sid,
+                      const int *__restrict__ plof, int nk, int nb, int nsm, int npm, int n3,
+                      long long nr, long long rows, const RegTw<T, N> tw) {
+  extern __shared__ float4 yx_smem[];
+  cx<T> *yb = reinterpret_cast<cx<T> *>(yx_smem);
+  constexpr int PS = yx_pstride<N>();
+  const long long row = row_of_block();
+  if (row >= rows) return;  // uniform over the CTA
+  const int k = (int)((row / (2 * nb)) % nk);
+  const int j3c = blockIdx.x * kJ3;
+  const int np = __ldg(npl + k);
+  const long long n23 = (long long)N * n3;
+  const cx<T> *src = i1 + row * nsm * (long long)n3;
+  // Y lines of the sphere's planes: (plane p, z plane j3c + jj)
+  for (int t = threadIdx.x; t < np * kJ3; t += blockDim.x) {
+    const int p = t / kJ3, jj = t - p * kJ3, j3 = j3c + jj;
+    const bool in = j3 < n3;
+    const int *sd = sid + ((long long)k * npm + p) * N;
+    cx<T> a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int st = __ldg(sd + j);
+      a[j] = (in && st >= 0) ? src[(long long)st * n3 + j3] : czero<T>();
+    }
+    RegPlan<N>::template run<T, +1>(a, tw);
+    cx<T> *o = yb + p * PS + jj;
+#pragma unroll
+    for (int j = 0; j < N; ++j) o[j * kJ3] = a[j];
+  }
+  __syncthreads();
+  // X lines of the box: (j2, z plane j3c + jj)
+  const int *po = plof + (long long)k * N;
+  cx<T> *dst = xr + row * nr;
+  for (int t = threadIdx.x; t < N * kJ3; t += blockDim.x) {
+    const int j2 = t / kJ3, jj = t - j2 * kJ3, j3 = j3c + jj;
+    cx<T> a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int p = __ldg(po + j);
+      a[j] = p >= 0 ? yb[p * PS + j2 * kJ3 + jj] : czero<T>();
+    }
+    RegPlan<N>::template run<T, +1>(a, tw);
+    if (j3 < n3) {
+      cx<T> *o = dst + (long long)j2 * n3 + j3;
+#pragma unroll
+      for (int j = 0; j < N; ++j) o[j * n23] = a[j];
+    }
+  }
+}
+
+// Forward: X lines of the box (keeping the sphere's planes) into shared memory, then
+// the Y lines of those planes written to the sphere's sticks.
+template <class T, int N>
+__global__ void __launch_bounds__(kYXMaxThreads)
+    fwd_xy_reg_kernel(const cx<T> *__restrict__ xr, cx<T> *__restrict__ i1,
+                      const int *__restrict__ npl, const int *__restrict__ sid,
+                      const int *__restrict__ plof, int nk, int nb, int nsm, int npm, int n3,
+                      long long nr, long long rows, const RegTw<T, N> tw) {
+  extern __shared__ float4 yx_smem[];
+  cx<T> *yb = reinterpret_cast<cx<T> *>(yx_smem);
+  constexpr int PS = yx_pstride<N>();
+  const long long row = row_of_block();
+  if (row >= rows) return;  // uniform over the CTA
+  const int k = (int)((row / (2 * nb)) % nk);
+  const int j3c = blockIdx.x * kJ3;
+  const int np = __ldg(npl + k);
+  const long long n23 = (long long)N * n3;
+  const int *po = plof + (long long)k * N;
+  const cx<T> *src = xr + row * nr;
+  for (int t = threadIdx.x; t < N * kJ3; t += blockDim.x) {
+    const int j2 = t / kJ3, jj = t - j2 * kJ3, j3 = j3c + jj;
+    const bool in = j3 < n3;
+    const cx<T> *sp = src + (long long)j2 * n3 + j3;
+    cx<T> a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = in ? sp[j * n23] : czero<T>();
+    RegPlan<N>::template run<T, -1>(a, tw);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int p = __ldg(po + j);
+      if (p >= 0) yb[p * PS + j2 * kJ3 + jj] = a[j];
+    }
+  }
+  __syncthreads();
+  cx<T> *dst = i1 + row * nsm * (long long)n3;
+  for (int t = threadIdx.x; t < np * kJ3; t += blockDim.x) {
+    const int p = t / kJ3, jj = t - p * kJ3, j3 = j3c + jj;
+    const cx<T> *ys = yb + p * PS + jj;
+    cx<T> a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = ys[j * kJ3];
+    RegPlan<N>::template run<T, -1>(a, tw);
+    if (j3 < n3) {
+      const int *sd = sid + ((long long)k * npm + p) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int st = __ldg(sd + j);
+        if (st >= 0) dst[(long long)st * n3 + j3] = a[j];
+      }
+    }
+  }
+}
+
 template <class T> const cx<T> *tw_of(const AxisPlan &a) {
   if constexpr (sizeof(T) == 8)
     return a.tw_d;
@@ -847,7 +969,51 @@ template <class T> bool use_reg_lines(int n) {
   return reg_fft_length(n) && (sizeof(T) == 4 || n <= 45);
 }
 
+// Shared memory of a fused Y + X CTA (the sphere's planes of kJ3 z planes).
+size_t yx_smem_bytes(const QSlot &s, size_t elem) {
+  int ps = 0;
+  switch (s.fft[0]) {
+    case 12: ps = yx_pstride<12>(); break;
+    case 16: ps = yx_pstride<16>(); break;
+    case 24: ps = yx_pstride<24>(); break;
+    case 36: ps = yx_pstride<36>(); break;
+    case 45: ps = yx_pstride<45>(); break;
+    case 48: ps = yx_pstride<48>(); break;
+    default: return 0;
+  }
+  return (size_t)s.nplane_max * ps * elem;
+}
+
+// Launch KERNEL<T, N> with the fused Y + X CTA shape for the register-line lengths.
+#define TDLZ_YX_LAUNCH(n, KERNEL, rows, ...)                                              \
+  switch (n) {                                                                           \
+    case 12: TDLZ_YX_ONE(12, KERNEL, rows, __VA_ARGS__); break;                          \
+    case 16: TDLZ_YX_ONE(16, KERNEL, rows, __VA_ARGS__); break;                          \
+    case 24: TDLZ_YX_ONE(24, KERNEL, rows, __VA_ARGS__); break;                          \
+    case 36: TDLZ_YX_ONE(36, KERNEL, rows, __VA_ARGS__); break;                          \
+    case 45: TDLZ_YX_ONE(45, KERNEL, rows, __VA_ARGS__); break;                          \
+    case 48: if constexpr (sizeof(T) == 4) { TDLZ_YX_ONE(48, KERNEL, rows, __VA_ARGS__); } break; \
+    default: break;                                                                      \
+  }
+#define TDLZ_YX_ONE(NN, KERNEL, rows, ...)                                                \
+  {                                                                                      \
+    const size_t sm = yx_smem_bytes(s, sizeof(cx<T>));                                   \
+    set_smem(KERNEL<T, NN>, sm);                                                         \
+    KERNEL<T, NN><<<grid_rows((unsigned)((n3 + kJ3 - 1) / kJ3), rows), yx_threads<NN>(), sm, \
+                    st>>>(__VA_ARGS__, regtw<T, NN>());                                  \
+  }
+
 }  // namespace
+
+template <class T> bool yx_fused_supported(const QSlot &s) {
+  const size_t sm = yx_smem_bytes(s, sizeof(cx<T>));
+  // FP64 lines of 45 points spill in the fused kernels (two lines' worth of addressing)
+  const int nmax = sizeof(T) == 8 ? 36 : 48;
+  return s.fft[0] == s.fft[1] && s.fft[0] <= nmax && use_reg_lines<T>(s.fft[0]) && sm > 0 &&
+         sm <= 227 * 1024;
+}
+template bool yx_fused_supported<float>(const QSlot &);
+template bool yx_fused_supported<double>(const QSlot &);
 
 void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq) {
   const int n1 = s.fft[0], n2 = s.fft[1], n3 = s.fft[2];
@@ -1043,6 +1209,14 @@ void pipeline_inverse(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *xr, cx<T> *
     }
     TDLZ_LAUNCH_CHECK();
   }
+  if (sizeof(T) == 4 ? s.yx32 : s.yx64) {
+    // sticks in, real-space grids out; the planes stay on chip
+    ProfScope ps(ctx.prof, st, ST_FFT_INV, wk.S1 * c + wk.G * c, wk.y_flops + wk.x_flops);
+    TDLZ_YX_LAUNCH(n1, inv_yx_reg_kernel, rows, i1, xr, s.pl_n.as<int>(), s.st_id.as<int>(),
+                   s.pl_of.as<int>(), s.nk, s.nb, nsm, npm, n3, s.nr, rows);
+    TDLZ_LAUNCH_CHECK();
+    return;
+  }
   // sticks in, planes out and back in, real-space grids out
   ProfScope ps(ctx.prof, st, ST_FFT_INV, wk.S1 * c + 2 * wk.S2 * c + wk.G * c,
                wk.y_flops + wk.x_flops);
@@ -1106,6 +1280,14 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
           const_cast<cx<T> *>(xr), ur, vloc, bf, v, s.nk, s.nb, s.nr, nvec);
       TDLZ_LAUNCH_CHECK();
     }
+    if (sizeof(T) == 4 ? s.yx32 : s.yx64) {
+      // real-space grids in, sticks out; the planes stay on chip
+      ProfScope ps(ctx.prof, st, ST_FFT_FWD, wk.G * c + wk.S1 * c, wk.x_flops + wk.y_flops);
+      TDLZ_YX_LAUNCH(n1, fwd_xy_reg_kernel, rows, xr, i1, s.pl_n.as<int>(), s.st_id.as<int>(),
+                     s.pl_of.as<int>(), s.nk, s.nb, nsm, npm, n3, s.nr, rows);
+      TDLZ_LAUNCH_CHECK();
+      ok = true;
+    } else {
     ProfScope ps(ctx.prof, st, ST_FFT_FWD, wk.G * c + 2 * wk.S2 * c + wk.S1 * c,
                  wk.x_flops + wk.y_flops);
     tuned_lines(ctx, "fwd_x", c, n1, n23, rows, [&](int rt) {
@@ -1130,6 +1312,7 @@ void pipeline_forward(Context &ctx, QSlot &s, const cx<T> *x, const cx<T> *xr, c
           i2, i1, s.pl_n.as<int>(), s.st_id.as<int>(), s.nk, s.nb, nsm, npm, n2, n3, rows,
           stages(s.plan.ax[1]), tw_of<T>(s.plan.ax[1]));
       TDLZ_LAUNCH_CHECK();
+    }
     }
   } else {
     // X pass with the products formed in shared memory (no separate product pass)

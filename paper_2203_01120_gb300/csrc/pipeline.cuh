@@ -10,6 +10,11 @@ namespace tdlz {
 // Stick / plane tables of every k+q sphere (host-built at load, uploaded).
 void build_stick_tables(QSlot &s, const std::vector<int> &idx_kq);
 
+// True when the Y and X line passes of precision T can run fused, one CTA per (row,
+// chunk of z planes) with the sphere's planes in shared memory (square x-y grid of a
+// register-line length, the planes within the shared-memory limit): no plane buffer.
+template <class T> bool yx_fused_supported(const QSlot &s);
+
 // x (nvec stacked BR vectors) -> xr (real space, [nvec*rows][Nr]); i1, i2 are the
 // stick and plane scratch ([rows][nstick_max][n3], [rows][nplane_max][n2][n3]).
 template <class T>

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <vector>
@@ -29,6 +30,24 @@ inline const char *stage_name(int s) {
                                     "product", "fft_fwd", "gather", "vnl", "pc", "lanczos"};
   return (s >= 0 && s < ST_COUNT) ? n[s] : "?";
 }
+
+// NVTX range names of the stages (host-side ranges around each stage's launches, seen
+// by an attached profiler; without one the calls return at once)
+inline const char *stage_range(int s) {
+  static const char *n[ST_COUNT] = {"tdlz/scatter", "tdlz/fft_inv", "tdlz/density",
+                                    "tdlz/hartree", "tdlz/potential", "tdlz/product",
+                                    "tdlz/fft_fwd", "tdlz/gather", "tdlz/vnl", "tdlz/pc",
+                                    "tdlz/lanczos"};
+  return (s >= 0 && s < ST_COUNT) ? n[s] : "tdlz/?";
+}
+
+// RAII NVTX range on the calling host thread.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 extern std::atomic<long long> g_launches;
 
@@ -72,7 +91,8 @@ struct Profiler {
   }
 };
 
-// RAII scope: records an event pair around the enclosed launches when profiling.
+// RAII scope: an NVTX range named after the stage around the enclosed launches, and
+// when profiling an event pair on the stream.
 struct ProfScope {
   Profiler *p;
   cudaStream_t st;
@@ -80,6 +100,7 @@ struct ProfScope {
   long long l0;
   ProfScope(Profiler &prof, cudaStream_t s, int stage, double bytes, double flops)
       : p(prof.on ? &prof : nullptr), st(s) {
+    nvtxRangePushA(stage_range(stage));
     l0 = g_launches.load();
     if (!p) return;
     r.stage = stage;
@@ -90,6 +111,7 @@ struct ProfScope {
     cudaEventRecord(r.a, st);
   }
   ~ProfScope() {
+    nvtxRangePop();
     if (!p) return;
     cudaEventRecord(r.b, st);
     r.launches = (int)(g_launches.load() - l0);

@@ -22,15 +22,15 @@ __global__ void spectrum_kernel(SpecArgs a) {
   int iw = (int)(tid - (long long)c * a.nomega);
   int m = a.steps[c];
   if (a.itermax0 > 0 && a.itermax0 < m) m = a.itermax0;
-  double2 *out = a.chi + ((long long)c * 3) * a.nomega + iw;
+  double2 *out = a.chi + ((long long)c * a.nl) * a.nomega + iw;
   if (m <= 0) {
-    for (int l = 0; l < 3; ++l) out[(long long)l * a.nomega] = make_double2(0, 0);
+    for (int l = 0; l < a.nl; ++l) out[(long long)l * a.nomega] = make_double2(0, 0);
     return;
   }
   const double2 *al = a.alpha + (long long)c * a.cap;
   const double *be = a.beta + (long long)c * a.cap;
   const double2 *ga = a.gamma + (long long)c * a.cap;
-  const double2 *zz = a.z + (long long)c * 3 * a.cap;
+  const double2 *zz = a.z + (long long)c * a.nl * a.cap;
   double om = a.start + a.step * iw;
   double2 zw = make_double2(om, a.eta);
   // Extrapolated tail (Sec. 3.3): coefficients m..itermax-1 are the means of the
@@ -77,10 +77,10 @@ __global__ void spectrum_kernel(SpecArgs a) {
     double2 bg = make_double2(be[m - 1] * ga[m - 1].x, be[m - 1] * ga[m - 1].y);
     tail = make_double2(bg.x * g.x - bg.y * g.y, bg.x * g.y + bg.y * g.x);
   }
-  double2 acc[3];
-  tridiag_chi(m, a.cap, al, be, ga, zz, zw, tail, a.scratch, nthr, tid, acc);
+  double2 acc[4];
+  tridiag_chi(m, a.cap, al, be, ga, zz, zw, tail, a.scratch, nthr, tid, a.nl, acc);
   double s = a.wk[c] * a.n0[c];
-  for (int l = 0; l < 3; ++l)
+  for (int l = 0; l < a.nl; ++l)
     out[(long long)l * a.nomega] = make_double2(s * acc[l].x, s * acc[l].y);
 }
 

@@ -11,12 +11,13 @@ struct SpecArgs {
   const double2 *alpha;  // [nchain][cap]
   const double *beta;    // [nchain][cap]
   const double2 *gamma;  // [nchain][cap]
-  const double2 *z;      // [nchain][3][cap]
+  const double2 *z;      // [nchain][nl][cap]
+  int nl;                // left vectors per chain: 3 (spin) or 4 (spin and charge)
   const double *n0, *wk; // [nchain]
   double start, step, eta;
   int itermax0, itermax, extrap;  // itermax0 <= 0: all computed; extrap 0 no, 1 constant, 2 osc
   double2 *scratch;      // [4][cap][nchain*nomega]
-  double2 *chi;          // [nchain][3][nomega]
+  double2 *chi;          // [nchain][nl][nomega]
 };
 
 void launch_spectrum(cudaStream_t st, const SpecArgs &a);

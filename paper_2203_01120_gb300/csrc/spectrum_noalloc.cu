@@ -30,7 +30,7 @@ __global__ void spectrum_noalloc_kernel(int nchain, int nomega, int cap, const i
                                         const double2 *alpha, const double *beta,
                                         const double2 *gamma, const double2 *z, const double *n0,
                                         const double *wk, double start, double step, double eta,
-                                        int w0, int nw, double2 *scratch, double2 *chi) {
+                                        int w0, int nw, int nl, double2 *scratch, double2 *chi) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nthr = (long long)nchain * nw;
   if (tid >= nthr) return;
@@ -38,20 +38,20 @@ __global__ void spectrum_noalloc_kernel(int nchain, int nomega, int cap, const i
   int iw = w0 + (int)(tid - (long long)c * nw);
   int m = steps[c];  // read on the device: clamped to [0, cap]
   if (m > cap) m = cap;
-  double2 *out = chi + ((long long)c * 3) * nomega + iw;
+  double2 *out = chi + ((long long)c * nl) * nomega + iw;
   if (m <= 0) {
-    for (int l = 0; l < 3; ++l) out[(long long)l * nomega] = make_double2(0, 0);
+    for (int l = 0; l < nl; ++l) out[(long long)l * nomega] = make_double2(0, 0);
     return;
   }
   const double2 *al = alpha + (long long)c * cap;
   const double *be = beta + (long long)c * cap;
   const double2 *ga = gamma + (long long)c * cap;
-  const double2 *zz = z + (long long)c * 3 * cap;
-  double2 acc[3];
+  const double2 *zz = z + (long long)c * nl * cap;
+  double2 acc[4];
   tridiag_chi(m, cap, al, be, ga, zz, make_double2(start + step * iw, eta), make_double2(0, 0),
-              scratch, nthr, tid, acc);
+              scratch, nthr, tid, nl, acc);
   double s = wk[c] * n0[c];
-  for (int l = 0; l < 3; ++l) out[(long long)l * nomega] = make_double2(s * acc[l].x, s * acc[l].y);
+  for (int l = 0; l < nl; ++l) out[(long long)l * nomega] = make_double2(s * acc[l].x, s * acc[l].y);
 }
 
 // Device address of the scratch on the current device; looked up once per device.
@@ -75,6 +75,8 @@ void spectrum_noalloc(Context &ctx, const tdlz_coeffs *c, const tdlz_spectrum_pa
                       double *chi, int nomega) {
   TDLZ_REQUIRE(c && sp && chi, TDLZ_ERR_ARG, "NULL coefficients, parameters or chi");
   TDLZ_REQUIRE(c->nchain >= 1 && c->nsteps >= 1, TDLZ_ERR_ARG, "empty coefficient set");
+  TDLZ_REQUIRE(c->ncomp == 0 || c->ncomp == 3 || c->ncomp == 4, TDLZ_ERR_ARG,
+               "ncomp must be 0 or 3 (spin) or 4 (spin and charge)");
   TDLZ_REQUIRE(c->steps && c->alpha && c->beta && c->gamma && c->z && c->n0 && c->wk,
                TDLZ_ERR_ARG, "NULL coefficient array");
   TDLZ_REQUIRE(sp->step > 0 && sp->end >= sp->start && std::isfinite(sp->eta) && sp->eta > 0,
@@ -103,7 +105,7 @@ void spectrum_noalloc(Context &ctx, const tdlz_coeffs *c, const tdlz_spectrum_pa
         c->nchain, nomega, c->nsteps, c->steps, reinterpret_cast<const double2 *>(c->alpha),
         c->beta, reinterpret_cast<const double2 *>(c->gamma),
         reinterpret_cast<const double2 *>(c->z), c->n0, c->wk, sp->start * conv, sp->step * conv,
-        sp->eta * conv, w0, n, scratch, reinterpret_cast<double2 *>(chi));
+        sp->eta * conv, w0, n, c->ncomp == 4 ? 4 : 3, scratch, reinterpret_cast<double2 *>(chi));
     TDLZ_LAUNCH_CHECK();
   }
 }

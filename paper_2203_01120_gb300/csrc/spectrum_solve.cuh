@@ -23,11 +23,11 @@ __device__ __forceinline__ double2 spec_cdiv(double2 a, double2 b) {
 // super-diagonal).  The eliminated rows d, du, du2, b of thread tid go to
 // scratch[(q cap + j) nthr + tid], q = 0..3, so that every step's accesses of the
 // nthr threads are coalesced.  The back substitution accumulates
-// acc[l] = sum_i conj(z^l_i) x_i (zz = z of the chain, [3][cap]).
+// acc[l] = sum_i conj(z^l_i) x_i for l < nl (zz = z of the chain, [nl][cap], nl <= 4).
 __device__ __forceinline__ void tridiag_chi(int m, int cap, const double2 *al, const double *be,
                                             const double2 *ga, const double2 *zz, double2 zw,
                                             double2 tail, double2 *scratch, long long nthr,
-                                            long long tid, double2 (&acc)[3]) {
+                                            long long tid, int nl, double2 (&acc)[4]) {
   double2 *sd = scratch, *sdu = scratch + (long long)cap * nthr,
           *sdu2 = scratch + 2LL * cap * nthr, *sb = scratch + 3LL * cap * nthr;
   // A = zw - T: d_j = zw - alpha_j, dl_j = -beta_j (A[j+1][j]), du_j = -gamma_j (A[j][j+1])
@@ -74,14 +74,14 @@ __device__ __forceinline__ void tridiag_chi(int m, int cap, const double2 *al, c
     sb[o] = b;
   }
   double2 x1 = make_double2(0, 0), x2 = make_double2(0, 0);  // x_{i+1}, x_{i+2}
-  for (int l = 0; l < 3; ++l) acc[l] = make_double2(0, 0);
+  for (int l = 0; l < 4; ++l) acc[l] = make_double2(0, 0);
   for (int i = m - 1; i >= 0; --i) {
     long long o = (long long)i * nthr + tid;
     double2 bi = sb[o], dui = sdu[o], du2i = sdu2[o];
     double2 num = make_double2(bi.x - (dui.x * x1.x - dui.y * x1.y) - (du2i.x * x2.x - du2i.y * x2.y),
                                bi.y - (dui.x * x1.y + dui.y * x1.x) - (du2i.x * x2.y + du2i.y * x2.x));
     double2 xi = spec_cdiv(num, sd[o]);
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < nl; ++l) {
       double2 zv = zz[(long long)l * cap + i];
       acc[l].x += zv.x * xi.x + zv.y * xi.y;
       acc[l].y += zv.x * xi.y - zv.y * xi.x;

@@ -77,14 +77,17 @@ CONFIGS = {
     # batch sets its own cutoff (c5_ecut) so that the k+q spheres hold 10000-13000 PW
     "C5": Config("C5", _hex(13.0, 38.0), (45, 45, 144), 12.7, (4, 4, 1), 70, (0.0625, 0, 0),
                  "hex", seed=1005, alat=13.0),
-    # a spontaneously magnetic model for the Goldstone check: one electron per cell bound
-    # in a deep Gaussian well (an isolated "atom"), so that the self-consistent Slater
-    # exchange polarises it fully without an external field; the atom's p projectors
-    # (lambda L_z sigma_z / 2) sit off the well's centre so that spin-orbit coupling
-    # reaches the occupied state
-    "CG": Config("CG", _cubic(8.0), (16, 16, 16), 3.8553, (1, 1, 1), 1, (0.02, 0, 0), "cubic",
-                 v_sigma=0.02, b_noncollinear=0.0, seed=1007, alat=8.0, natom=1,
-                 well_depth=3.0, well_width=1.0, well_shifts=((0.9, 0.6, 0.4),)),
+    # a spontaneously magnetic model for the Goldstone check: two electrons per cell bound
+    # in two deep Gaussian wells 3.5 bohr apart, polarised in parallel by the
+    # self-consistent Slater exchange without an external field; the atom's p projectors
+    # (lambda L_z sigma_z / 2, lambda = 0.9 Ha) sit 0.7 bohr off the first well so that
+    # spin-orbit coupling reaches the occupied states.  The cutoff lies halfway between
+    # two shells of |G|^2 (2 ecut = 12.5 (2 pi / a)^2), so the k+q spheres equal the k
+    # sphere for |q| < 0.06 (2 pi / a) and L changes smoothly with q there.
+    "CG": Config("CG", _cubic(8.0), (16, 16, 16), 3.8553, (1, 1, 1), 2, (0.01, 0, 0), "cubic",
+                 v_sigma=0.02, b_noncollinear=0.0, lam_so_scale=3.0, seed=1007, alat=8.0,
+                 natom=1, well_depth=3.0, well_width=1.0,
+                 well_shifts=((0.7, 0.0, 0.0), (-2.8, 0.0, 0.0))),
 }
 
 

@@ -74,8 +74,8 @@ def test_tensor_core_wait_expiry_reported_then_recovered(torch, monkeypatch):
 
 def _group_offsets(image, nchain, ngroup):
     """Byte offset of each group's vector slots in a restart image (header: 8-byte magic
-    and six ints; then (q-slot, mu) per chain and the step of each group)."""
-    return struct.calcsize("8s6i") + 8 * nchain + 4 * ngroup
+    and seven ints; then (q-slot, mu) per chain and the step of each group)."""
+    return struct.calcsize("8s7i") + 8 * nchain + 4 * ngroup
 
 
 def test_non_finite_chain_stops_alone(torch, ctx):
