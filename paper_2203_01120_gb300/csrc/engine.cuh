@@ -90,6 +90,7 @@ template <class T> struct Workspace {
   DevBuf i1;    // stick scratch: [rows][nstick_max][n3]; plane stages [rows][n3][nstick_max]
   DevBuf i2;    // staged pipeline: [rows][nplane_max][n2][n3] plane scratch
   int nvec_cap = 0;  // stacked vectors the buffers above are sized for
+  int ns_cap = 1;    // staged pipeline: vectors per sub-batch its grids are sized for
   bool ready = false;
 };
 

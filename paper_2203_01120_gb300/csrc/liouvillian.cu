@@ -616,21 +616,28 @@ double staged_vector_bytes(const QSlot &s, size_t c) {
   return (double)s.rows() * per_row * (double)c;
 }
 
-// Largest number of stacked vectors in one pass of the staged pipeline: all nvec where
-// their buffers take at most a tenth of the device memory, else the largest count that
-// does (at least one).  Non-decreasing in nvec: the workspace is sized by it.
+// Stacked vectors the staged pipeline's buffers are sized for, decided when they are
+// allocated: all nvec where they take at most 70% of the memory then free (and at most
+// half the device), else the largest count that does (at least one).  The count
+// changes no result (every vector's stages are independent of the others'), only how
+// often the orbitals U(r) are read per pass; q-slots allocated later see what is left.
 int staged_cap(const QSlot &s, size_t c, int nvec) {
-  int n = (int)std::floor(0.1 * (double)s.dev_total / staged_vector_bytes(s, c));
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_b = 0;
+  }
+  const double budget = std::min(0.5 * (double)s.dev_total, 0.7 * (double)free_b);
+  int n = (int)std::floor(budget / staged_vector_bytes(s, c));
   n = std::max(1, std::min(n, nvec));
   if (s.staged_sub_env > 0) n = std::min(n, s.staged_sub_env);
   return n;
 }
 
 // Vectors per sub-batch of a pass over nvec stacked vectors: the sub-batches balanced
-// under staged_cap (never above it).  Every vector's stages are independent of the
-// others', so the sub-batches change no result.
-int staged_sub(const QSlot &s, size_t c, int nvec) {
-  const int n = staged_cap(s, c, nvec);
+// under the workspace's capacity ns (never above it).
+int staged_sub(int ns, int nvec) {
+  const int n = std::max(1, std::min(ns, nvec));
   const int nbatch = (nvec + n - 1) / n;
   return (nvec + nbatch - 1) / nbatch;
 }
@@ -657,7 +664,13 @@ void alloc_workspace(QSlot &s, int nvec) {
     w.hgrid.alloc(nv * (size_t)s.nr * c);
   } else {
     // the real-space stages run over sub-batches of at most ns stacked vectors
+    // release the old grids first so that the free memory the capacity is sized by
+    // counts them
+    w.xr.reset();
+    w.i2.reset();
+    w.i1.reset();
     const size_t ns = (size_t)staged_cap(s, c, nvec);
+    w.ns_cap = (int)ns;
     const bool fused = sizeof(T) == 4 ? s.yx32 : s.yx64;
     w.xr.alloc(ns * s.rows() * s.nr * c);
     if (fused)
@@ -945,7 +958,7 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     const char *sub_env = std::getenv("TDLZ_STAGED_SUB");
     s.staged_sub_env = sub_env ? std::max(0, std::atoi(sub_env)) : 0;
     const char *yx_env = std::getenv("TDLZ_YX_FUSED");
-    const bool yx_on = yx_env && yx_env[0] == '1';
+    const bool yx_on = !(yx_env && yx_env[0] == '0');
     s.yx32 = yx_on && yx_fused_supported<float>(s);
     s.yx64 = yx_on && yx_fused_supported<double>(s);
     const char *pl_env = std::getenv("TDLZ_PLANES");
@@ -1076,6 +1089,7 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
     TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
     d.us.reset();
     d.ur.reset();
+    d.uvec.reset();  // the chains' left vectors are read in FP32 only
     s.mixed_only = true;
   }
   TDLZ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1219,7 +1233,7 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
   } else {
     cx<T> *xr = w.xr.template as<cx<T>>();
     cx<T> *i2 = w.i2.template as<cx<T>>();
-    const int nsub = staged_sub(s, sizeof(cx<T>), nvec);
+    const int nsub = staged_sub(w.ns_cap, nvec);
     for (int v0 = 0; v0 < nvec; v0 += nsub) {
       // vectors v0 .. v0 + m - 1: their grids, plane and stick buffers fill the workspace
       const int m = std::min(nsub, nvec - v0);

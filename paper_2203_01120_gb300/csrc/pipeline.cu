@@ -1006,11 +1006,11 @@ size_t yx_smem_bytes(const QSlot &s, size_t elem) {
 }  // namespace
 
 template <class T> bool yx_fused_supported(const QSlot &s) {
+  // FP32 only: the FP64 path is bound by the FP64 pipe, and its fused lines (176-255
+  // registers, spilling at 45 points) ran the C2 step 10% slower than the separate passes
+  if (sizeof(T) == 8) return false;
   const size_t sm = yx_smem_bytes(s, sizeof(cx<T>));
-  // FP64 lines of 45 points spill in the fused kernels (two lines' worth of addressing)
-  const int nmax = sizeof(T) == 8 ? 36 : 48;
-  return s.fft[0] == s.fft[1] && s.fft[0] <= nmax && use_reg_lines<T>(s.fft[0]) && sm > 0 &&
-         sm <= 227 * 1024;
+  return s.fft[0] == s.fft[1] && use_reg_lines<T>(s.fft[0]) && sm > 0 && sm <= 227 * 1024;
 }
 template bool yx_fused_supported<float>(const QSlot &);
 template bool yx_fused_supported<double>(const QSlot &);

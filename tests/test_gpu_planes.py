@@ -202,3 +202,35 @@ def test_staged_sub_batches_change_no_result(torch, monkeypatch, prec):
     for other in out[1:]:
         for key in ("alpha", "beta", "gamma", "z", "n0", "steps_done", "status"):
             assert np.array_equal(out[0][key], other[key]), key
+
+
+@pytest.mark.parametrize("case", ["C0K", "C1", "C3grid"])
+def test_fused_yx_passes_equal_separate_passes(torch, monkeypatch, case):
+    """The staged pipeline's fused Y + X line kernels (one CTA per row and chunk of z
+    planes, the planes in shared memory; the default, TDLZ_YX_FUSED=0 turns it off)
+    transform every line with the same plan in the same order as the separate Y and X
+    passes: L x in FP64 and mixed
+    precision and the Lanczos coefficients are bit for bit the same."""
+    from paper_2203_01120_gb300 import Context, TDLZ_MIXED
+    gs = c3_small() if case == "C3grid" else ground_state(case)
+    x = random_br_vector(gs, seed=61)
+    out = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("TDLZ_YX_FUSED", env)
+        c = Context(0)
+        try:
+            q = load(c, gs, monkeypatch, planes=False)
+            ys = [apply_gpu(torch, c, q, x), apply_gpu(torch, c, q, x, mixed=True),
+                  apply_gpu(torch, c, q, x, adjoint=True)]
+            chains = c.lanczos_run([q, q], [0, 2], 8, "nh", TDLZ_MIXED)
+        finally:
+            c.close()
+        out.append((ys, chains))
+    (y0, c0), (y1, c1) = out
+    for a, b in zip(y0, y1):
+        assert np.array_equal(a, b)
+    for key in ("alpha", "beta", "gamma", "z"):
+        assert np.array_equal(c0[key], c1[key]), key
+    if case != "C3grid":
+        ref = liouvillian(case).apply(x)
+        assert rel(y1[0], ref) <= 1e-12
