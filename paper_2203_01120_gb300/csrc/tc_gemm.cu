@@ -10,7 +10,8 @@
 // Im C = A_rot . B_int where A_rot = (-a.y, a.x) per element, so one real GEMM
 // with the 2M rows [A_int; A_rot] against the rows of B gives both parts
 // (2M <= 128 = the MMA's M).  The batches that share one A (b = a + j amod) are
-// stacked as the N rows of one tile (N <= 256).
+// stacked as the N rows of one tile (N <= 256).  For 64 < M <= 128 the roles swap
+// (tc_gemm_tnt_kernel): 128 stacked B rows are the MMA's M, the 2M rows its N.
 //
 // 3xTF32: every FP32 operand x is split into hi = tf32(x) and lo = tf32(x - hi)
 // while it is staged into shared memory, and D += Ahi Bhi + Ahi Blo + Alo Bhi
@@ -133,7 +134,8 @@ struct TcArgs {
   int ntot, nt;    // stacked B rows (nj * N) and rows per N tile (multiple of 16)
   int ntiles, nsplit, kt_per_split, nkt;
   uint32_t tmem_cols;
-  float *part;     // [nsplit][amod][ntiles][128][nt]
+  float *part;     // [nsplit][amod][ntiles][128][nt]; transposed form [..][128][nm]
+  int nm;          // transposed form: the MMA's N, 2M rounded up to 16
 };
 
 __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs g) {
@@ -323,6 +325,208 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tn_kernel(const TcArgs 
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(g.tmem_cols));
+}
+
+// Transposed form for 64 < M <= 128 (2M rows do not fit the MMA's M): the MMA's M = 128
+// stacked B rows (R = j N + n of the batches b = a + j amod sharing A), its N = the 2M
+// rows [A_int; A_rot] rounded up to 16 (<= 256), so D[R][m] = Re C[m][n] and
+// D[R][M + m] = Im C[m][n] of TMEM lane R.  Staging, pipeline and the bounded waits are
+// those of tc_gemm_tn_kernel with the operands' roles exchanged.
+__global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_tnt_kernel(const TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, abort_it;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nm = g.nm;
+  const uint32_t lboX = 16 * 128, lboA = (uint32_t)(nm / 8) * 128;
+  const uint32_t xTile = 128 * kKT * 4, aTile = (uint32_t)nm * kKT * 4;
+  const uint32_t stage_bytes = 2 * xTile + 2 * aTile;
+  // CTA coordinates: x = 128-row tile of the stacked B rows, y = A batch, z = K split
+  const int tile = blockIdx.x, a = blockIdx.y, z = blockIdx.z;
+  const int kt0 = z * g.kt_per_split;
+  const int kt1 = min(g.nkt, kt0 + g.kt_per_split);
+  const int nloc = kt1 - kt0;
+  for (uint32_t i = tid; i < 2 * stage_bytes / 16; i += blockDim.x)
+    reinterpret_cast<float4 *>(tc_smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+    abort_it = nloc;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(g.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = (1u << 4)                           // D: F32
+                         | (2u << 7) | (2u << 10)             // A, B: TF32
+                         | ((uint32_t)(nm >> 3) << 17)        // N >> 3
+                         | ((uint32_t)(128 >> 4) << 24);      // M >> 4
+  const float2 *Ab = g.A + (long long)a * g.sA;
+  constexpr int kWarpsPerRow = kChunks / 4;
+  const int lane = tid & 31;
+  const int sub = (lane >> 3) + 4 * (warp % kWarpsPerRow);
+  const int rbase = (warp / kWarpsPerRow) * 8 + (lane & 7);
+  const int rstep = kRowStep;
+  constexpr int kX = 128 / kRowStep, kA = 128 / kRowStep;  // rows per thread (M <= 128)
+  float4 vx[kX], va[kA];
+  auto load_tile = [&](int t) {
+    const long long kc = (long long)(kt0 + t) * (kKT / 2) + 2 * sub;
+#pragma unroll
+    for (int i = 0; i < kX; ++i) {
+      const int r = rbase + i * rstep;
+      const int R = tile * 128 + r;
+      vx[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (R < g.ntot && kc < g.K) {
+        const int j = R / g.N, n = R - j * g.N;
+        const float2 *row =
+            g.B + (long long)(a + (long long)j * g.amod) * g.sB + (long long)n * g.ldb;
+        const float2 t0 = __ldg(row + kc);
+        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
+        vx[i] = make_float4(t0.x, t0.y, t1.x, t1.y);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kA; ++i) {
+      const int m = rbase + i * rstep;
+      va[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < g.M && kc < g.K) {
+        const float2 *row = Ab + (long long)m * g.lda;
+        const float2 t0 = __ldg(row + kc);
+        const float2 t1 = kc + 1 < g.K ? __ldg(row + kc + 1) : make_float2(0.f, 0.f);
+        va[i] = make_float4(t0.x, t0.y, t1.x, t1.y);
+      }
+    }
+  };
+  if (nloc > 0) load_tile(0);
+  for (int it = 0; it < nloc; ++it) {
+    const int s = it & 1;
+    if (it >= 2) {
+      if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((it - 2) >> 1) & 1))) {
+        abort_flag = 1;
+        abort_it = it;
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    unsigned char *st = tc_smem + (size_t)s * stage_bytes;
+    unsigned char *Xhi = st, *Xlo = st + xTile, *Ahi = st + 2 * xTile, *Alo = Ahi + aTile;
+#pragma unroll
+    for (int i = 0; i < kX; ++i) {
+      const int r = rbase + i * rstep;
+      float4 hi, lo;
+      split4(vx[i], hi, lo);
+      *reinterpret_cast<float4 *>(Xhi + tile_off(r, sub, lboX)) = hi;
+      *reinterpret_cast<float4 *>(Xlo + tile_off(r, sub, lboX)) = lo;
+    }
+#pragma unroll
+    for (int i = 0; i < kA; ++i) {
+      const int m = rbase + i * rstep;
+      if (m < g.M) {
+        float4 hi, lo;
+        split4(va[i], hi, lo);
+        *reinterpret_cast<float4 *>(Ahi + tile_off(m, sub, lboA)) = hi;
+        *reinterpret_cast<float4 *>(Alo + tile_off(m, sub, lboA)) = lo;
+        split4(make_float4(-va[i].y, va[i].x, -va[i].w, va[i].z), hi, lo);
+        *reinterpret_cast<float4 *>(Ahi + tile_off(g.M + m, sub, lboA)) = hi;
+        *reinterpret_cast<float4 *>(Alo + tile_off(g.M + m, sub, lboA)) = lo;
+      }
+    }
+    if (it + 1 < nloc) load_tile(it + 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t xh = smem_u32(Xhi), xl = smem_u32(Xlo), ah = smem_u32(Ahi),
+                     al = smem_u32(Alo);
+#pragma unroll
+      for (int ks = 0; ks < kKT / 8; ++ks) {
+        const uint32_t ox = 2 * ks * lboX, oa = 2 * ks * lboA;
+        const uint64_t dxh = smem_desc(xh + ox, lboX, 128), dxl = smem_desc(xl + ox, lboX, 128);
+        const uint64_t dah = smem_desc(ah + oa, lboA, 128), dal = smem_desc(al + oa, lboA, 128);
+        const uint32_t acc0 = (it > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dxh), "l"(dah), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.eq.u32 p, 1, 1;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %4, %5, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dxh), "l"(dal), "r"(idesc), "l"(dxl), "l"(dah));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar[s])));
+    }
+  }
+  quiesce(mbar, abort_flag, abort_it, nloc);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = !abort_flag && nloc > 0;
+  if (!ok && tid == 0 && abort_flag) atomicExch(&g_tc_timeout, 1);
+  // epilogue: warp w reads TMEM lanes 32 (w & 3) .. + 31 (stacked rows R), the two warps
+  // of a quarter take alternate 8-column chunks of the nm columns
+  const int quarter = warp & 3;
+  const int row = 32 * quarter + (tid & 31);
+  float *out = g.part + ((((long long)z * gridDim.y + a) * g.ntiles + tile) * 128 + row) * nm;
+  for (int c0 = 8 * (warp >> 2); c0 < nm; c0 += 16) {
+    uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (ok) {
+      const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+    }
+    float4 *o = reinterpret_cast<float4 *>(out + c0);
+    if (ok) {
+      o[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
+                         __uint_as_float(r[3]));
+      o[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]),
+                         __uint_as_float(r[7]));
+    } else {
+      o[0] = o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(g.tmem_cols));
+}
+
+// C[b*sC + m*ldcm + n*ldcn] = sum_z (part[z][a][t][rr][m], part[z][a][t][rr][M+m]) with
+// b = a + j amod, stacked row R = j N + n = 128 t + rr (the transposed form's partials).
+__global__ void tc_reduce_t_kernel(const float *__restrict__ part, float2 *__restrict__ C, int M,
+                                   int N, int amod, int nj, int ntiles, int nm, int nsplit,
+                                   long long sC, long long ldcm, long long ldcn) {
+  const long long total = (long long)amod * nj * M * N;
+  const long long zstride = (long long)amod * ntiles * 128 * nm;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / ((long long)M * N);
+    const int rem = (int)(e - b * M * N);
+    const int m = rem / N, n = rem - m * N;
+    const int a = (int)(b % amod), j = (int)(b / amod);
+    const int R = j * N + n, t = R >> 7, rr = R & 127;
+    const float *p = part + ((((long long)a * ntiles + t) * 128) + rr) * nm;
+    float re = 0.f, im = 0.f;
+    for (int zz = 0; zz < nsplit; ++zz) {
+      re += p[(long long)zz * zstride + m];
+      im += p[(long long)zz * zstride + M + m];
+    }
+    C[b * sC + m * ldcm + n * ldcn] = make_float2(re, im);
+  }
 }
 
 // C[b*sC + m*ldcm + n*ldcn] = sum_z (part[z][a][t][m][col], part[z][a][t][M+m][col])
@@ -557,12 +761,66 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_gemm_nn_kernel(const NnArgs 
                  "r"(g.tmem_cols));
 }
 
+// 64 < M <= 128: the transposed form (tc_gemm_tnt_kernel), same contract as tc_gemm_tn.
+bool tc_gemm_tn_transposed(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda,
+                           long long sA, int amod, const float2 *B, long long ldb, long long sB,
+                           float2 *C, long long sC, long long ldcm, long long ldcn, int M, int N,
+                           long long K, int batch) {
+  TcArgs g{};
+  g.A = A;
+  g.lda = lda;
+  g.sA = sA;
+  g.amod = amod;
+  g.B = B;
+  g.ldb = ldb;
+  g.sB = sB;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.nj = batch / amod;
+  g.ntot = g.nj * N;
+  g.ntiles = (g.ntot + 127) / 128;
+  g.nt = 128;
+  g.nm = (2 * M + 15) / 16 * 16;
+  g.nkt = (int)((K + kKT / 2 - 1) / (kKT / 2));
+  const int ctas = amod * g.ntiles;
+  const size_t per_split = (size_t)amod * g.ntiles * 128 * g.nm * sizeof(float);
+  const long long fit = (long long)(partbuf.bytes / per_split);
+  if (fit < 1) return false;
+  long long ns = std::max(1, std::min(g.nkt, (4 * 152 + ctas - 1) / ctas));
+  ns = std::min(ns, fit);
+  g.kt_per_split = (int)((g.nkt + ns - 1) / ns);
+  g.nsplit = (g.nkt + g.kt_per_split - 1) / g.kt_per_split;
+  g.tmem_cols = 32;
+  while (g.tmem_cols < (uint32_t)g.nm) g.tmem_cols *= 2;
+  g.part = partbuf.as<float>();
+  // no more CTAs per SM than the 512 TMEM columns hold (ask for enough shared memory that
+  // one more would not fit), so that no CTA waits in tcgen05.alloc
+  const int cap = (int)(512 / g.tmem_cols);
+  const size_t smem = std::max(2 * (2 * (size_t)128 * kKT * 4 + 2 * (size_t)g.nm * kKT * 4),
+                               (size_t)(233472 / (cap + 1)));
+  TDLZ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_tnt_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.ntiles, amod, g.nsplit);
+  tc_gemm_tnt_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(g);
+  TDLZ_LAUNCH_CHECK();
+  const long long total = (long long)batch * M * N;
+  tc_reduce_t_kernel<<<blocks_for(total), 256, 0, ctx.stream>>>(g.part, C, M, N, amod, g.nj,
+                                                                 g.ntiles, g.nm, g.nsplit, sC,
+                                                                 ldcm, ldcn);
+  TDLZ_LAUNCH_CHECK();
+  return true;
+}
+
 }  // namespace
 
 bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
                 int amod, const float2 *B, long long ldb, long long sB, float2 *C, long long sC,
                 long long ldcm, long long ldcn, int M, int N, long long K, int batch) {
-  if (2 * M > 128 || M < 1 || N < 1 || K < 1 || amod < 1 || batch % amod != 0) return false;
+  if (M > 128 || M < 1 || N < 1 || K < 1 || amod < 1 || batch % amod != 0) return false;
+  if (2 * M > 128)
+    return tc_gemm_tn_transposed(ctx, partbuf, A, lda, sA, amod, B, ldb, sB, C, sC, ldcm, ldcn,
+                                 M, N, K, batch);
   TcArgs g;
   g.A = A;
   g.lda = lda;
@@ -609,8 +867,19 @@ bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long
                 const float2 *B, long long ldb, long long sB, int bmod, const float2 *In,
                 float2 *Out, long long ldo, long long sO, int rows, long long ncol, int K,
                 float alpha, int batch, int neg_from, int neg_mod) {
-  if (rows < 1 || 2 * rows > 256 || K < 1 || ncol < 1 || batch < 1 || bmod < 1 || neg_mod < 1)
-    return false;
+  if (rows < 1 || K < 1 || ncol < 1 || batch < 1 || bmod < 1 || neg_mod < 1) return false;
+  if (2 * rows > 256) {
+    // more rows than the MMA's N holds (the V_NL update with 2 N_b > 128 rows): row
+    // blocks of at most 128, each an independent launch on its own rows of A, In and Out
+    for (int r0 = 0; r0 < rows; r0 += 128) {
+      const int nr = std::min(128, rows - r0);
+      if (!tc_gemm_nn(ctx, A + (long long)r0 * sar, sA, sar, sak, B, ldb, sB, bmod,
+                      In + (long long)r0 * ldo, Out + (long long)r0 * ldo, ldo, sO, nr, ncol, K,
+                      alpha, batch, neg_from, neg_mod))
+        return false;
+    }
+    return true;
+  }
   NnArgs g;
   g.A = A;
   g.sA = sA;

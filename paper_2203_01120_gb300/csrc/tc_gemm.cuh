@@ -6,8 +6,10 @@
 namespace tdlz {
 
 // C[b*sC + m*ldcm + n*ldcn] = sum_k conj(A[(b % amod)*sA + m*lda + k]) B[b*sB + n*ldb + k]
-// for b < batch (complex FP32, FP32 accumulation).  Returns false, launching nothing,
-// for shapes outside the kernel (2M > 128, batch not a multiple of amod, or partbuf
+// for b < batch (complex FP32, FP32 accumulation).  M <= 64 stacks the batches sharing
+// A as the MMA's N (2M rows of A as its M); 64 < M <= 128 runs the transposed form (128
+// stacked B rows as the MMA's M, the 2M rows of A as its N).  Returns false, launching
+// nothing, for shapes outside both (M > 128, batch not a multiple of amod, or partbuf
 // smaller than one split); the caller then uses the CUDA-core GEMM.
 bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
                 int amod, const float2 *B, long long ldb, long long sB, float2 *C, long long sC,
@@ -17,7 +19,7 @@ bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, l
 //                                           B[(b % bmod)*sB + k*ldb + n])
 // for b < batch, r < rows, n < ncol, k < K (complex FP32, 3xTF32 on the tensor cores,
 // FP32 accumulation); sg_b = -1 where b % neg_mod >= neg_from, else +1.  In may equal
-// Out (in-place update).  Returns false, launching nothing, for 2 rows > 256.
+// Out (in-place update).  More than 128 rows run as row blocks of at most 128.
 bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long long sak,
                 const float2 *B, long long ldb, long long sB, int bmod, const float2 *In,
                 float2 *Out, long long ldo, long long sO, int rows, long long ncol, int K,

@@ -358,3 +358,33 @@ def test_restart_rejects_mismatched_image(torch, ctx):
     with pytest.raises(TdlzError):
         c.restore(image)
     c.close()
+
+
+def test_tensor_core_reductions_above_64_bands(torch, monkeypatch):
+    """P_c's reduction <U_kq|h> with more than 64 occupied bands (2M > 128 rows, the
+    CrI3-shaped workloads' 70) runs the transposed tensor-core form (the MMA's M = 128
+    stacked rows of h, its N = the 2M rows of [Re; Im] of U_kq): the C1 grid with 72
+    random orthonormal occupied states, mixed L x against the oracle (<= 2e-5) and against
+    the CUDA-core contractions (TDLZ_TC=0, <= 1e-5)."""
+    from paper_2203_01120_gb300 import Context, TDLZ_MIXED
+    from synth import make_ground_state
+    from oracle.liouvillian import Liouvillian
+    gs = make_ground_state("C1", solver="random", nocc=72)
+    x = random_br_vector(gs, seed=71)
+    ref = Liouvillian(gs).apply(x)
+    ys = []
+    for tc in ("1", "0"):
+        monkeypatch.setenv("TDLZ_TC", tc)
+        c = Context(0)
+        try:
+            q = c.load_ground_state(gs)
+            xt = torch.as_tensor(x, dtype=torch.complex64, device="cuda").contiguous()
+            yt = torch.zeros_like(xt)
+            c.apply_liouvillian(q, xt, yt, False, TDLZ_MIXED)
+            c.synchronize()
+            ys.append(yt.cpu().numpy().astype(np.complex128))
+        finally:
+            c.close()
+    y_tc, y_cc = ys
+    assert np.linalg.norm(y_tc - ref) <= 2e-5 * np.linalg.norm(ref)
+    assert np.linalg.norm(y_tc - y_cc) <= 1e-5 * np.linalg.norm(ref)
