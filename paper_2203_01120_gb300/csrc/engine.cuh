@@ -56,6 +56,16 @@ struct DevBuf {
   template <class U> U *as() const { return reinterpret_cast<U *>(p); }
 };
 
+// TF32 operand images of a constant matrix B[g][k][n] (tc_gemm.cu): for every 128-column
+// tile and K tile of 8 complex k, the hi and lo parts in the canonical shared-memory
+// layout the update GEMM's MMA reads, so that the GEMM moves them with bulk copies and
+// converts nothing.  Twice the FP32 matrix in size, rounded up to whole tiles.
+struct TcImage {
+  DevBuf buf;
+  int G = 0, K = 0, nct = 0, nkt = 0;
+  long long ncol = 0;
+};
+
 // Ground-state data of one precision (T = double or float) on the device.
 template <class T> struct SlotData {
   DevBuf ukq;    // [2][nk][nb][2][npwx] occupied k+q spinors (P_c)
@@ -72,6 +82,9 @@ template <class T> struct SlotData {
   DevBuf wk;     // [nk]   (real)
   DevBuf uvec;   // [3][BR] u^lambda = J sigma^lambda U (unprojected)
   DevBuf us;     // plane stages: [2][nk][nb][2][n3][n1*n2 (even)] U(r) in z-major slabs
+  // FP32 tensor-core path: operand images of U_kq (G = 2 nk, K = nb, 2 npwx columns) and
+  // of the projectors (G = nk, K = nproj, npwx columns) for the P_c and V_NL updates
+  TcImage ukq_img, beta_img;
   bool ready = false;
 };
 
@@ -136,6 +149,7 @@ struct QSlot {
   bool mixed_only = false;
   size_t dev_total = 0;    // device memory (bytes): sizes the staged pipeline's sub-batches
   int staged_sub_env = 0;  // TDLZ_STAGED_SUB=n: at most n stacked vectors per staged pass
+  bool tc_images = true;    // the updates read precomputed operand images (TcImage)
   bool tensor_gemm = true;  // FP32 V_NL / P_c reductions and updates on tcgen05 (tc_gemm.cu)
   FFTPlan plan;
   SlotData<double> d64;

@@ -974,6 +974,9 @@ void load_slot(Context &ctx, QSlot &s, const tdlz_ground_state *gs) {
   // TDLZ_TC=0 keeps the V_NL / P_c reductions and updates on the CUDA-core GEMMs (A/B timing)
   const char *tc_env = std::getenv("TDLZ_TC");
   s.tensor_gemm = !(tc_env && tc_env[0] == '0');
+  // TDLZ_TC_IMG=0 keeps the updates on the register-staged GEMM (no operand images)
+  const char *img_env = std::getenv("TDLZ_TC_IMG");
+  s.tc_images = !(img_env && img_env[0] == '0');
   up(s.perm, perm.data(), perm.size() * sizeof(int));
   up(s.iperm, iperm.data(), iperm.size() * sizeof(int));
   up(s.idx_k, idx_k.data(), idx_k.size() * sizeof(int));
@@ -1125,6 +1128,14 @@ void ensure_precision(Context &ctx, QSlot &s) {
       convert_buf<float>(ctx, d.vhfac, f.vhfac);
       convert_buf<float>(ctx, d.wk, f.wk);
       convert_buf<float>(ctx, d.uvec, f.uvec);
+      if (s.tensor_gemm && s.tc_images) {
+        const long long bstride = (long long)s.nb * 2 * s.npwx;
+        tc_image_build(ctx, f.ukq_img, f.ukq.as<float2>(), 2LL * s.npwx, bstride, 2 * s.nk,
+                       s.nb, 2LL * s.npwx);
+        if (s.nproj > 0)
+          tc_image_build(ctx, f.beta_img, f.beta.as<float2>(), s.npwx,
+                         (long long)s.nproj * s.npwx, s.nk, s.nproj, s.npwx);
+      }
       f.ready = true;
     }
   }
@@ -1293,10 +1304,15 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
     TDLZ_LAUNCH_CHECK();
     bool tcu = false;
     if constexpr (sizeof(T) == 4)
-      if (s.tensor_gemm)
-        tcu = tc_gemm_nn(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<float2>(),
-                         npwx, (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_,
-                         1.f, batch, batch, 1 << 30);
+      if (s.tensor_gemm) {
+        if (d.beta_img.buf.p)
+          tcu = tc_gemm_nn_img(ctx, d.beta_img, w.part, dm, (long long)2 * nb * np_, np_, 1, h,
+                               h, npwx, bstride, 2 * nb, 1.f, batch, batch, 1 << 30);
+        if (!tcu)
+          tcu = tc_gemm_nn(ctx, dm, (long long)2 * nb * np_, np_, 1,
+                           d.beta.template as<float2>(), npwx, (long long)np_ * npwx, nk, h, h,
+                           npwx, bstride, 2 * nb, npwx, np_, 1.f, batch, batch, 1 << 30);
+      }
     if (!tcu)
       gemm_nn<T>(ctx, dm, (long long)2 * nb * np_, np_, 1, d.beta.template as<cx<T>>(), npwx,
                  (long long)np_ * npwx, nk, h, h, npwx, bstride, 2 * nb, npwx, np_, T(1), batch,
@@ -1319,9 +1335,15 @@ void apply_liouvillian(Context &ctx, QSlot &s, const cx<T> *x, cx<T> *y, int nve
                  (long long)nb * nb, nb, 1, nb, nb, 2LL * npwx, batch);
     bool tcu = false;
     if constexpr (sizeof(T) == 4)
-      if (s.tensor_gemm)
-        tcu = tc_gemm_nn(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h,
-                         y, 2LL * npwx, bstride, nb, 2LL * npwx, nb, -1.f, batch, nk, batch1);
+      if (s.tensor_gemm) {
+        if (d.ukq_img.buf.p)
+          tcu = tc_gemm_nn_img(ctx, d.ukq_img, w.part, ov, (long long)nb * nb, 1, nb, h, y,
+                               2LL * npwx, bstride, nb, -1.f, batch, nk, batch1);
+        if (!tcu)
+          tcu = tc_gemm_nn(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1,
+                           h, y, 2LL * npwx, bstride, nb, 2LL * npwx, nb, -1.f, batch, nk,
+                           batch1);
+      }
     if (!tcu)
       gemm_nn<T>(ctx, ov, (long long)nb * nb, 1, nb, ukq, 2LL * npwx, bstride, batch1, h, y,
                  2LL * npwx, bstride, nb, 2LL * npwx, nb, T(-1), batch, nk, batch1);

@@ -23,7 +23,13 @@
 // (A batch, N tile, K split); a two-stage pipeline overlaps the staging of K tile
 // t+1 (global loads, TF32 split) with the MMAs of tile t; the partial sums go to
 // a split-K buffer that a second kernel reduces in fixed order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 
 #include "engine.cuh"
 #include "tc_gemm.cuh"
@@ -812,6 +818,384 @@ bool tc_gemm_tn_transposed(Context &ctx, DevBuf &partbuf, const float2 *A, long 
   return true;
 }
 
+// ---------------------------------------------------------------------------------
+// Update GEMM from operand images: the bulk-copy / TMA form of tc_gemm_nn_kernel.
+//
+// The MMA operands of every K tile are kept in global memory already split into TF32
+// hi and lo parts and laid out as the canonical K-major shared-memory tiles the MMA
+// reads (core matrices of 8 rows x 16 bytes, chunks 16 rows-groups apart):
+//   A operand: 128 columns n of the constant matrix B[g][k][n] (the occupied k+q
+//              states, the projectors), built once per ground state (nn_aimg_kernel);
+//   B operand: the 2R rows (Re, Im) built from A[b][r][k], per call (nn_bimg_kernel).
+// A CTA then only moves bytes and issues MMAs: one thread copies the K tiles into a
+// ring of S shared-memory stages with 1-D bulk copies (cp.async.bulk) and issues the
+// MMAs of each stage as it lands; a stage is refilled once the MMAs that read it have
+// committed.  Meanwhile the other threads prefetch the CTA's In tile into L2 for the
+// epilogue (or, optionally, one tensor copy, cp.async.bulk.tensor over the 3-D map
+// [batch][R][2 ncol], brings it into shared memory at launch).  Values, MMA order and
+// epilogue arithmetic are those of tc_gemm_nn_kernel, so the result is the same bit
+// for bit.
+constexpr uint32_t kAImgTile = 2 * 128 * 16 * 4;  // A-operand image of one K tile, hi + lo
+constexpr int kNnMaxStages = 8;
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// tiled tensor copy of the box at (x, y, z) of a 3-D map (x in elements of dimension 0)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// img[(g nct + ct) nkt + kt][hl][c][nl] (16-byte entries) = TF32 split (hl = 0: hi,
+// 1: lo) of (B[g][k][n], B[g][k + 1][n]) with k = 8 kt + 2 c, n = 128 ct + nl; zero
+// outside K x ncol.  Consecutive threads take consecutive columns (coalesced).
+__global__ void nn_aimg_kernel(const float2 *__restrict__ B, long long ldb, long long sB, int G,
+                               int K, long long ncol, int nct, int nkt, float4 *__restrict__ img) {
+  const long long total = (long long)G * nct * nkt * 512;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nl = (int)(e & 127), c = (int)((e >> 7) & 3);
+    const long long tile = e >> 9;
+    const int kt = (int)(tile % nkt);
+    const long long gc = tile / nkt;
+    const int ct = (int)(gc % nct);
+    const long long g = gc / nct;
+    const long long n = (long long)ct * 128 + nl;
+    const int k0 = 8 * kt + 2 * c;
+    float2 t0 = make_float2(0.f, 0.f), t1 = t0;
+    if (n < ncol) {
+      const float2 *col = B + g * sB + n;
+      if (k0 < K) t0 = col[(long long)k0 * ldb];
+      if (k0 + 1 < K) t1 = col[(long long)(k0 + 1) * ldb];
+    }
+    float4 hi, lo;
+    split4(make_float4(t0.x, t0.y, t1.x, t1.y), hi, lo);
+    float4 *o = img + tile * 1024 + c * 128 + nl;
+    o[0] = hi;
+    o[512] = lo;
+  }
+}
+
+// img[b nkt + kt][hl][c][row] (16-byte entries, nm rows): rows 2r and 2r + 1 hold the
+// TF32 split of (a0.x, -a0.y, a1.x, -a1.y) and (a0.y, a0.x, a1.y, a1.x) with
+// a0 = A[b][r][k0], a1 = A[b][r][k0 + 1], k0 = 8 kt + 2 c (zero beyond K); rows >= 2R
+// are zero.
+__global__ void nn_bimg_kernel(const float2 *__restrict__ A, long long sA, long long sar,
+                               long long sak, int R, int K, int nkt, int nm, long long batch,
+                               float4 *__restrict__ img) {
+  const int half = nm / 2;
+  const long long total = batch * nkt * 4 * half;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int rp = (int)(e % half);
+    long long t = e / half;
+    const int c = (int)(t & 3);
+    t >>= 2;  // b nkt + kt
+    const int kt = (int)(t % nkt);
+    const long long b = t / nkt;
+    float4 *o = img + t * (8LL * nm) + (long long)c * nm + 2 * rp;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rp >= R) {
+      o[0] = o[1] = o[4 * nm] = o[4 * nm + 1] = z4;
+      continue;
+    }
+    const int k0 = 8 * kt + 2 * c;
+    const float2 *row = A + b * sA + (long long)rp * sar;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+    if (k0 < K) a0 = row[(long long)k0 * sak];
+    if (k0 + 1 < K) a1 = row[(long long)(k0 + 1) * sak];
+    float4 hr, lr, hm, lm;
+    split4(make_float4(a0.x, -a0.y, a1.x, -a1.y), hr, lr);  // Re row
+    split4(make_float4(a0.y, a0.x, a1.y, a1.x), hm, lm);    // Im row
+    o[0] = hr;
+    o[1] = hm;
+    o[4 * nm] = lr;
+    o[4 * nm + 1] = lm;
+  }
+}
+
+struct NnImgArgs {
+  const unsigned char *aimg;  // [G][nct][nkt] A-operand K-tile images (kAImgTile bytes each)
+  const unsigned char *bimg;  // [batch][nkt] B-operand K-tile images (128 nm bytes each)
+  const float2 *In;           // read in the epilogue where the tensor copy is not used
+  float2 *Out;
+  long long ldo, sO, ncol;
+  int R, nm, nkt, nct, G, nj, S, in_tma;
+  float alpha;
+  int neg_from, neg_mod;
+  uint32_t tmem_cols, in_bytes, stage_bytes;
+};
+
+// One CTA per (batch b, 128-column tile); the CTAs of the batches b = g + j G that share
+// an A-operand image are consecutive in launch order (j fastest), so that the image is
+// read from L2 after the first of them.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_nn_img_kernel(const __grid_constant__ CUtensorMap tm_in, const NnImgArgs g) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t full[kNnMaxStages], empty[kNnMaxStages], inbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, n_commit;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  long long L = blockIdx.x;
+  const int j = (int)(L % g.nj);
+  L /= g.nj;
+  const int ct = (int)(L % g.nct);
+  const long long gi = L / g.nct;
+  const long long b = gi + (long long)j * g.G;
+  const uint32_t bop = 128u * (uint32_t)g.nm;
+  const int S = g.S;
+  unsigned char *in_s = tc_smem;               // [R][256 floats] In tile (tensor copy)
+  unsigned char *ring = tc_smem + g.in_bytes;  // S stages: A image, then B image
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&inbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+    n_commit = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(g.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const float2 *inb = g.In + b * g.sO;
+  if (!g.in_tma) {
+    // In is read in the epilogue: start pulling this tile's rows into L2 now
+    for (int e = tid; e < g.R * 8; e += kTcThreads) {
+      const long long n0 = (long long)ct * 128 + (e & 7) * 16;
+      if (n0 < g.ncol)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(inb + (long long)(e >> 3) * g.ldo + n0));
+    }
+  }
+  if (tid == 0) {
+    const unsigned char *abase = g.aimg + (gi * g.nct + ct) * g.nkt * (long long)kAImgTile;
+    const unsigned char *bbase = g.bimg + b * g.nkt * (long long)bop;
+    auto issue = [&](int t) {
+      const int s = t % S;
+      const uint32_t bar = smem_u32(&full[s]);
+      const uint32_t dst = smem_u32(ring + (size_t)s * g.stage_bytes);
+      mbar_expect_tx(bar, kAImgTile + bop);
+      bulk_g2s(dst, abase + (long long)t * kAImgTile, kAImgTile, bar);
+      bulk_g2s(dst + kAImgTile, bbase + (long long)t * bop, bop, bar);
+    };
+    if (g.in_tma) {
+      const uint32_t bar = smem_u32(&inbar);
+      mbar_expect_tx(bar, g.in_bytes);
+      tma_load_3d(smem_u32(in_s), &tm_in, ct * 256, 0, (int)b, bar);
+    }
+    int issued = 0;
+    while (issued < min(S, g.nkt)) issue(issued++);
+    const uint32_t idesc = (1u << 4)                           // D: F32
+                           | (2u << 7) | (2u << 10)             // A, B: TF32
+                           | ((uint32_t)(g.nm >> 3) << 17)      // N >> 3
+                           | ((uint32_t)(kNnM >> 4) << 24);     // M >> 4
+    const uint32_t lboA = (kNnM / 8) * 128, lboB = (uint32_t)g.nm * 16;
+    bool ok = true;
+    int committed = 0;
+    for (int it = 0; it < g.nkt; ++it) {
+      const int s = it % S;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / S) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(ring + (size_t)s * g.stage_bytes), al = ah + kAImgTile / 2;
+      const uint32_t bh = ah + kAImgTile, bl = bh + bop / 2;
+#pragma unroll
+      for (int ks = 0; ks < kNnKT / 8; ++ks) {
+        const uint32_t oa = 2 * ks * lboA, ob = 2 * ks * lboB;
+        const uint64_t dah = smem_desc(ah + oa, lboA, 128), dal = smem_desc(al + oa, lboA, 128);
+        const uint64_t dbh = smem_desc(bh + ob, lboB, 128), dbl = smem_desc(bl + ob, lboB, 128);
+        const uint32_t acc0 = (it > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.eq.u32 p, 1, 1;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %4, %5, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbl), "r"(idesc), "l"(dal), "l"(dbh));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[s])));
+      committed = it + 1;
+      // refill the stage of the previous tile once its MMAs have committed (the stage
+      // of this tile is still being read); issued == it - 1 + S here
+      if (it >= 1 && issued < g.nkt) {
+        const int p = it - 1;
+        if (!mbar_wait(smem_u32(&empty[p % S]), (uint32_t)((p / S) & 1))) {
+          ok = false;
+          break;
+        }
+        issue(issued++);
+      }
+    }
+    // quiesce: every copy issued lands, and the last commit (which covers every MMA
+    // issued before it) completes, before TMEM is read or the CTA's memory released.
+    // The last S copies issued are the newest of their stages, so their phases are
+    // unambiguous; waits after an expiry ignore test injections.
+    if (!ok)
+      for (int u = max(0, issued - S); u < issued; ++u)
+        mbar_wait_raw(smem_u32(&full[u % S]), (uint32_t)((u / S) & 1));
+    if (committed > 0) {
+      const int last = committed - 1;
+      const uint32_t bar = smem_u32(&empty[last % S]), par = (uint32_t)((last / S) & 1);
+      if (ok && !mbar_wait(bar, par)) ok = false;
+      if (!ok) mbar_wait_raw(bar, par);
+    }
+    if (g.in_tma) {
+      const uint32_t bar = smem_u32(&inbar);
+      if (ok && !mbar_wait(bar, 0)) ok = false;
+      if (!ok) mbar_wait_raw(bar, 0);
+    }
+    abort_flag = ok ? 0 : 1;
+    n_commit = committed;
+  }
+  __syncthreads();
+  const bool ok = !abort_flag && n_commit == g.nkt;
+  if (tid == 0 && abort_flag) atomicExch(&g_tc_timeout, 1);
+  if (ok) {
+    // completed phases: these waits return at once and order the MMAs' TMEM writes and
+    // the tensor copy's shared-memory writes before this thread's reads
+    const int last = g.nkt - 1;
+    mbar_wait_raw(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1));
+    if (g.in_tma) mbar_wait_raw(smem_u32(&inbar), 0);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // epilogue (as tc_gemm_nn_kernel): warp w reads lane quarter w & 3 (32 consecutive
+  // columns n); the two warps of a quarter take alternate 16-column TMEM blocks
+  const int quarter = warp & 3;
+  const int nl = 32 * quarter + lane;
+  const long long n = (long long)ct * kNnM + nl;
+  const bool nv = n < g.ncol;
+  const float sg = (b % g.neg_mod) >= g.neg_from ? -1.f : 1.f;
+  const float2 *inrow = inb + n;
+  float2 *outb = g.Out + b * g.sO + n;
+  for (int j0 = 16 * (warp >> 2); j0 < 2 * g.R; j0 += 32) {
+    const int r0 = j0 >> 1;
+    if (!ok) break;  // TMEM is read only after the last commit's barrier completed
+    float2 iv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      iv[u] = make_float2(0.f, 0.f);
+      if (r0 + u < g.R) {
+        if (g.in_tma)
+          iv[u] = *reinterpret_cast<const float2 *>(in_s + (size_t)(r0 + u) * 1024 + nl * 8);
+        else if (nv)
+          iv[u] = inrow[(long long)(r0 + u) * g.ldo];
+      }
+    }
+    uint32_t v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (nv) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (r0 + u >= g.R) break;
+        const float re = __uint_as_float(v[2 * u]), im = __uint_as_float(v[2 * u + 1]);
+        outb[(long long)(r0 + u) * g.ldo] =
+            make_float2(sg * (iv[u].x + g.alpha * re), sg * (iv[u].y + g.alpha * im));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(g.tmem_cols));
+}
+
+// ---------------------------------------------------------------------------------
+// Host side of the tensor-copy GEMMs.
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// FP32 tensor map of `rank` dimensions (dims[0] contiguous; strides[i] in bytes between
+// consecutive elements of dimension i + 1) with the given box and zero fill outside;
+// false where the base or a stride is not 16-byte aligned or the encoder refuses it
+bool encode_map(CUtensorMap &m, int rank, const void *base, const uint64_t *dims,
+                const uint64_t *strides, const uint32_t *box) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn || reinterpret_cast<uintptr_t>(base) % 16) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) {
+      if (strides[i] % 16) return false;
+      st[i] = strides[i];
+    }
+  }
+  return fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d,
+            st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// CTAs per SM the image GEMM sizes its shared memory for (TDLZ_NN_CTAS=1, 2 or 3; default
+// 3): fewer CTAs keep more K tiles in flight each
+int nn_img_ctas_per_sm() {
+  const char *e = std::getenv("TDLZ_NN_CTAS");
+  return (e && e[0] >= '1' && e[0] <= '3') ? e[0] - '0' : 3;
+}
+
+// whether the image GEMM fetches its In tile with a tensor copy where it can
+// (TDLZ_NN_IN_TMA=1); by default it is read in the epilogue after an L2 prefetch, which
+// leaves the shared memory to a deeper ring (at C2 shapes 122 against 131 us per launch)
+bool nn_img_in_tma() {
+  const char *e = std::getenv("TDLZ_NN_IN_TMA");
+  return e && e[0] == '1';
+}
+
 }  // namespace
 
 bool tc_gemm_tn(Context &ctx, DevBuf &partbuf, const float2 *A, long long lda, long long sA,
@@ -913,6 +1297,101 @@ bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long
   dim3 grid((unsigned)((ncol + kNnM - 1) / kNnM), (unsigned)batch);
   tc_gemm_nn_kernel<<<grid, kTcThreads, smem, ctx.stream>>>(g);
   TDLZ_LAUNCH_CHECK();
+  return true;
+}
+
+void tc_image_build(Context &ctx, TcImage &im, const float2 *B, long long ldb, long long sB,
+                    int G, int K, long long ncol) {
+  TDLZ_REQUIRE(G >= 1 && K >= 1 && ncol >= 1, TDLZ_ERR_ARG, "operand image: empty matrix");
+  (void)tensor_map_encoder();  // resolve the encoder now, outside any stream capture
+  im.G = G;
+  im.K = K;
+  im.ncol = ncol;
+  im.nct = (int)((ncol + kNnM - 1) / kNnM);
+  im.nkt = (K + kNnKT / 2 - 1) / (kNnKT / 2);
+  const long long tiles = (long long)G * im.nct * im.nkt;
+  im.buf.alloc((size_t)tiles * kAImgTile);
+  nn_aimg_kernel<<<blocks_for(tiles * 512), 256, 0, ctx.stream>>>(B, ldb, sB, G, K, ncol, im.nct,
+                                                                  im.nkt, im.buf.as<float4>());
+  TDLZ_LAUNCH_CHECK();
+}
+
+bool tc_gemm_nn_img(Context &ctx, const TcImage &im, DevBuf &scratch, const float2 *A,
+                    long long sA, long long sar, long long sak, const float2 *In, float2 *Out,
+                    long long ldo, long long sO, int rows, float alpha, int batch, int neg_from,
+                    int neg_mod) {
+  const int G = im.G, nkt = im.nkt;
+  if (!im.buf.p || rows < 1 || batch < 1 || G < 1 || batch % G != 0 || neg_mod < 1) return false;
+  const bool tma_ok = nn_img_in_tma() && reinterpret_cast<uintptr_t>(In) % 16 == 0 &&
+                      ldo % 2 == 0 && sO % 2 == 0 && tensor_map_encoder() != nullptr;
+  const long long budget = 233472 / nn_img_ctas_per_sm() - 2048;  // per-CTA reserve + static
+  auto stages = [&](int R, bool tma) {
+    const int nm = (2 * R + 15) / 16 * 16;
+    const long long in_b = tma ? (long long)R * 1024 : 0;
+    return (int)std::min<long long>(std::min<long long>(nkt, kNnMaxStages),
+                                    (budget - in_b) / (kAImgTile + 128LL * nm));
+  };
+  // row blocks of at most 128 rows: as few as leave a ring of two stages (all K tiles
+  // where there are fewer)
+  int R = 0;
+  for (int nblk = (rows + 127) / 128; nblk <= rows; ++nblk) {
+    const int r = (rows + nblk - 1) / nblk;
+    if (stages(r, tma_ok) >= std::min(2, nkt)) {
+      R = r;
+      break;
+    }
+  }
+  if (R == 0) return false;
+  {
+    const int nm = (2 * R + 15) / 16 * 16;
+    if (scratch.bytes < (size_t)batch * nkt * 128 * nm) return false;
+  }
+  for (int r0 = 0; r0 < rows; r0 += R) {
+    const int nr = std::min(R, rows - r0);
+    NnImgArgs g{};
+    g.aimg = im.buf.as<unsigned char>();
+    g.bimg = scratch.as<unsigned char>();
+    g.In = In + (long long)r0 * ldo;
+    g.Out = Out + (long long)r0 * ldo;
+    g.ldo = ldo;
+    g.sO = sO;
+    g.ncol = im.ncol;
+    g.R = nr;
+    g.nm = (2 * nr + 15) / 16 * 16;
+    g.nkt = nkt;
+    g.nct = im.nct;
+    g.G = G;
+    g.nj = batch / G;
+    g.alpha = alpha;
+    g.neg_from = neg_from;
+    g.neg_mod = neg_mod;
+    g.tmem_cols = 32;
+    while (g.tmem_cols < (uint32_t)g.nm) g.tmem_cols *= 2;
+    alignas(64) CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    {
+      const uint64_t dims[3] = {2 * (uint64_t)im.ncol, (uint64_t)nr, (uint64_t)batch};
+      const uint64_t str[2] = {(uint64_t)ldo * 8, (uint64_t)sO * 8};
+      const uint32_t box[3] = {256, (uint32_t)nr, 1};
+      g.in_tma = tma_ok && encode_map(map, 3, g.In, dims, str, box);
+    }
+    g.in_bytes = g.in_tma ? (uint32_t)nr * 1024 : 0;
+    g.S = stages(nr, g.in_tma);
+    g.stage_bytes = kAImgTile + 128u * (uint32_t)g.nm;
+    nn_bimg_kernel<<<blocks_for((long long)batch * nkt * 2 * g.nm), 256, 0, ctx.stream>>>(
+        A + (long long)r0 * sar, sA, sar, sak, nr, im.K, nkt, g.nm, batch, scratch.as<float4>());
+    TDLZ_LAUNCH_CHECK();
+    // no more CTAs per SM than the 512 TMEM columns hold: ask for enough shared memory
+    // that one more would not fit either
+    const int cap = (int)(512 / g.tmem_cols);
+    const size_t smem = std::max((size_t)g.in_bytes + (size_t)g.S * g.stage_bytes,
+                                 (size_t)(233472 / (cap + 1)));
+    TDLZ_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_nn_img_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long nblocks = (long long)im.nct * batch;
+    tc_gemm_nn_img_kernel<<<(unsigned)nblocks, kTcThreads, smem, ctx.stream>>>(map, g);
+    TDLZ_LAUNCH_CHECK();
+  }
   return true;
 }
 

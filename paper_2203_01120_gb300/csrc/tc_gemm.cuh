@@ -25,6 +25,22 @@ bool tc_gemm_nn(Context &ctx, const float2 *A, long long sA, long long sar, long
                 float2 *Out, long long ldo, long long sO, int rows, long long ncol, int K,
                 float alpha, int batch, int neg_from, int neg_mod);
 
+// Builds the operand images (TcImage, engine.cuh) of the constant matrix B[g][k][n]
+// (g < G, k < K, n < ncol; row stride ldb, group stride sB).
+void tc_image_build(Context &ctx, TcImage &im, const float2 *B, long long ldb, long long sB,
+                    int G, int K, long long ncol);
+
+// tc_gemm_nn with B the matrix of `im` (bmod = im.G, K = im.K, ncol = im.ncol): the same
+// contract and, for the same operands, the same result bit for bit.  The per-call
+// B-operand images (the 2R rows built from A) go to `scratch`.  In is read in the epilogue
+// after an L2 prefetch (TDLZ_NN_IN_TMA=1: one tensor copy per CTA where its base and
+// strides are 16-byte aligned).  Returns false, launching nothing, where batch is not a
+// multiple of im.G or scratch is too small; the caller then uses tc_gemm_nn.
+bool tc_gemm_nn_img(Context &ctx, const TcImage &im, DevBuf &scratch, const float2 *A,
+                    long long sA, long long sar, long long sak, const float2 *In, float2 *Out,
+                    long long ldo, long long sO, int rows, float alpha, int batch, int neg_from,
+                    int neg_mod);
+
 // Throws TDLZ_ERR_TIMEOUT (and clears the flag) if a tensor-core GEMM gave up on an
 // mbarrier wait since the last check.  Synchronous.
 void tc_gemm_check();

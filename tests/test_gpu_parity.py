@@ -388,3 +388,94 @@ def test_tensor_core_reductions_above_64_bands(torch, monkeypatch):
     y_tc, y_cc = ys
     assert np.linalg.norm(y_tc - ref) <= 2e-5 * np.linalg.norm(ref)
     assert np.linalg.norm(y_tc - y_cc) <= 1e-5 * np.linalg.norm(ref)
+
+
+def _c3_grid_small():
+    from synth import make_ground_state
+    return make_ground_state("C3", solver="random", kgrid=(2, 1, 1), nocc=6)
+
+
+@pytest.mark.parametrize("ctas,in_tma", [("3", "0"), ("2", "0"), ("1", "0"), ("2", "1")])
+@pytest.mark.parametrize("case", ["C0K", "C1", "C1-72", "C3grid"])
+def test_update_gemm_images_equal_register_staging(torch, monkeypatch, case, ctas, in_tma):
+    """The tensor-core updates of V_NL and P_c read precomputed TF32 operand images with
+    bulk and tensor copies (the default; TDLZ_TC_IMG=0 keeps the register-staged kernel).
+    Same operand values, same MMA order, same epilogue: mixed L x, its adjoint and 6 NH
+    Lanczos steps (replayed from a captured graph) are bit for bit those of the
+    register-staged kernel.  The cases cover the In tile read in the epilogue after an L2
+    prefetch (the default) and fetched with one tensor copy per CTA (TDLZ_NN_IN_TMA=1:
+    P_c's rows always, V_NL's on the 45x45x144 grid, whose spheres have an even number of
+    plane waves per component), 72 bands (row blocks) and the shared-memory sizings for
+    one, two or three CTAs per SM (TDLZ_NN_CTAS; fewer CTAs keep more K tiles in
+    flight)."""
+    from paper_2203_01120_gb300 import Context, TDLZ_MIXED
+    from synth import make_ground_state
+    if case == "C3grid":
+        gs = _c3_grid_small()
+    elif case == "C1-72":
+        gs = make_ground_state("C1", solver="random", nocc=72)
+    else:
+        gs = ground_state(case)
+    x = random_br_vector(gs, seed=81)
+    monkeypatch.setenv("TDLZ_NN_CTAS", ctas)
+    monkeypatch.setenv("TDLZ_NN_IN_TMA", in_tma)
+    out = []
+    for img in ("0", "1"):
+        monkeypatch.setenv("TDLZ_TC_IMG", img)
+        c = Context(0)
+        try:
+            q = c.load_ground_state(gs)
+            ys = []
+            for adjoint in (False, True):
+                xt = torch.as_tensor(x, dtype=torch.complex64, device="cuda").contiguous()
+                yt = torch.zeros_like(xt)
+                c.apply_liouvillian(q, xt, yt, adjoint, TDLZ_MIXED)
+                c.synchronize()
+                ys.append(yt.cpu().numpy())
+            chains = c.lanczos_run([q, q], [0, 2], 6, "nh", TDLZ_MIXED)
+        finally:
+            c.close()
+        out.append((ys, chains))
+    (y0, c0), (y1, c1) = out
+    for a, b in zip(y0, y1):
+        assert np.array_equal(a, b)
+    for key in ("alpha", "beta", "gamma", "z"):
+        assert np.array_equal(c0[key], c1[key]), key
+
+
+def test_update_gemm_images_abort_path(torch, monkeypatch):
+    """Every bounded wait of the tensor-core GEMMs (including the image-fed update's
+    copy, MMA-commit and In waits) reports expiry once it has completed
+    (TDLZ_TEST_INJECT_TC_TIMEOUT large): each CTA drains its copies and MMAs, releases
+    TMEM and the call returns TDLZ_ERR_TIMEOUT; a new context (injection cleared) then
+    computes L x within the mixed tolerance of the oracle."""
+    from paper_2203_01120_gb300 import Context, TdlzError, TDLZ_MIXED
+    lv = liouvillian("C1")
+    x = random_br_vector(lv.gs, seed=83)
+
+    def apply(c, q):
+        xt = torch.as_tensor(x, dtype=torch.complex64, device="cuda").contiguous()
+        yt = torch.zeros_like(xt)
+        c.apply_liouvillian(q, xt, yt, False, TDLZ_MIXED)
+        c.synchronize()
+        return yt.cpu().numpy().astype(np.complex128)
+
+    monkeypatch.setenv("TDLZ_TC", "1")
+    monkeypatch.setenv("TDLZ_TEST_INJECT_TC_TIMEOUT", str(1 << 30))
+    c = Context(0)
+    try:
+        q = c.load_ground_state(lv.gs)
+        with pytest.raises(TdlzError) as e:
+            apply(c, q)
+        assert e.value.status == 7  # TDLZ_ERR_TIMEOUT
+    finally:
+        c.close()
+    monkeypatch.setenv("TDLZ_TEST_INJECT_TC_TIMEOUT", "0")
+    c = Context(0)
+    try:
+        q = c.load_ground_state(lv.gs)
+        ref = lv.apply(x)
+        assert np.linalg.norm(apply(c, q) - ref) <= 2e-5 * np.linalg.norm(ref)
+    finally:
+        c.close()
+
