@@ -527,6 +527,7 @@ __global__ void tc_reduce_t_kernel(const float *__restrict__ part, float2 *__res
     const int R = j * N + n, t = R >> 7, rr = R & 127;
     const float *p = part + ((((long long)a * ntiles + t) * 128) + rr) * nm;
     float re = 0.f, im = 0.f;
+#pragma unroll 8
     for (int zz = 0; zz < nsplit; ++zz) {
       re += p[(long long)zz * zstride + m];
       im += p[(long long)zz * zstride + M + m];
@@ -551,6 +552,7 @@ __global__ void tc_reduce_kernel(const float *__restrict__ part, float2 *__restr
     const int R = j * N + n, t = R / nt, col = R - t * nt;
     const float *p = part + (((long long)a * ntiles + t) * 128) * nt + col;
     float re = 0.f, im = 0.f;
+#pragma unroll 8
     for (int zz = 0; zz < nsplit; ++zz) {
       re += p[(long long)zz * zstride + (long long)m * nt];
       im += p[(long long)zz * zstride + (long long)(M + m) * nt];
@@ -1324,7 +1326,15 @@ bool tc_gemm_nn_img(Context &ctx, const TcImage &im, DevBuf &scratch, const floa
   if (!im.buf.p || rows < 1 || batch < 1 || G < 1 || batch % G != 0 || neg_mod < 1) return false;
   const bool tma_ok = nn_img_in_tma() && reinterpret_cast<uintptr_t>(In) % 16 == 0 &&
                       ldo % 2 == 0 && sO % 2 == 0 && tensor_map_encoder() != nullptr;
-  const long long budget = 233472 / nn_img_ctas_per_sm() - 2048;  // per-CTA reserve + static
+  // CTAs per SM: as asked, but no more than the 512 TMEM columns hold (the accumulator of
+  // 2R <= 256 columns is rounded up to a power of two)
+  int cps = nn_img_ctas_per_sm();
+  {
+    uint32_t cols = 32;
+    while (cols < (uint32_t)((2 * std::min(rows, 128) + 15) / 16 * 16)) cols *= 2;
+    cps = std::min(cps, (int)(512 / cols));
+  }
+  const long long budget = 233472 / cps - 2048;  // per-CTA reserve + static
   auto stages = [&](int R, bool tma) {
     const int nm = (2 * R + 15) / 16 * 16;
     const long long in_b = tma ? (long long)R * 1024 : 0;
